@@ -1,0 +1,160 @@
+"""Pins for the oracle's actions, heat bath and forces (CPU only).
+
+  * Heat bath: S(phi(chi)) = chi^dag chi for every term kind (the action and
+    the heat bath are computed by different routes).
+  * Determinant identities of mass preconditioning and polynomial filtering
+    (Section 2, Section 4.1): the Gaussian integrals of the PF-MP terms
+    multiply to det K_hat, checked densely on 2^4.
+  * Gauge invariance of every action term under random SU(3) transforms.
+  * Forces: central finite differences of the actions in extended precision
+    (long double, solves to 1e-18), step 1e-5, on links that include the
+    antiperiodic time boundary; tolerance 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice, su3, wilson, actions, force
+from oracle.cg import dense_matrix, vdot
+from oracle.poly import ChebyshevFilter
+from paper_1702_00124_gb300 import synthetic
+
+LD = np.clongdouble
+
+
+def _terms(kappa, kappa_h, n=4):
+    pf = ChebyshevFilter(n, 0.05, 5.0)
+    return [actions.term("plain", kappa),
+            actions.term("hasenbusch", kappa, kappa_h),
+            actions.term("poly", kappa_h, poly=pf),
+            actions.term("filtered", kappa_h, poly=pf)]
+
+
+@pytest.fixture(scope="module")
+def setup44():
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge_field(dims, 0.5, 41)
+    chi = lattice.mask(synthetic.spinor_field(dims, 42), dims, 0)
+    return dims, U, chi
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_heatbath_gives_chi_norm(setup44, i):
+    dims, U, chi = setup44
+    t = _terms(0.125, 0.115)[i]
+    phi = actions.heatbath(U, t, chi)
+    S, _ = actions.action(U, t, phi)
+    assert abs(S - vdot(chi, chi).real) < 1e-10 * vdot(chi, chi).real
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_gauge_invariance(setup44, i):
+    dims, U, chi = setup44
+    t = _terms(0.125, 0.115)[i]
+    g = synthetic.gauge_field(dims, 1.0, 77)[..., 1, :, :]
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[..., mu, :, :] = g @ U[..., mu, :, :] @ su3.dagger(lattice.shift(g, mu, +1))
+    phi = chi
+    phig = np.einsum("...ab,...sb->...sa", g, phi)
+    S1, _ = actions.action(U, t, phi)
+    S2, _ = actions.action(Ug, t, phig)
+    assert abs(S1 - S2) < 1e-11 * abs(S1)
+
+
+def test_pfmp_determinant_identity():
+    """det P(J)^-1 . det(P(J) J) . det(J K^-1)^-1 ... = det K_hat (PF-MP, Section 4.1):
+    the Gaussian integral of exp(-phi^dag A phi) is proportional to det A^-1."""
+    dims = (2, 2, 2, 2)
+    U = synthetic.gauge_field(dims, 0.6, 51)
+    k, kh = 0.12, 0.10
+    pf = ChebyshevFilter(6, 0.02, 6.0)
+    shp = lattice.shape(dims) + (4, 3)
+    sup = np.broadcast_to((lattice.parity(dims) == 0)[..., None, None], shp)
+    D = lambda op: dense_matrix(op, sup)[0]
+    K = D(lambda v: wilson.apply_Khat(U, v, k))
+    J = D(lambda v: wilson.apply_Khat(U, v, kh))
+    Mh = D(lambda v: wilson.apply_Mhat(U, v, kh))
+    PJ = D(lambda v: pf.apply(lambda w: wilson.apply_Khat(U, w, kh), v))
+    A_poly = PJ
+    A_filt = np.linalg.inv(PJ @ J)
+    A_hb = Mh @ np.linalg.inv(K) @ Mh.conj().T
+    logdet = lambda A: np.linalg.slogdet(A)[1]
+    lhs = -(logdet(A_poly) + logdet(A_filt) + logdet(A_hb))
+    assert abs(lhs - logdet(K)) < 1e-9 * abs(logdet(K))
+    # the dense P(J) matches the filter's scalar closed form on J's eigenvalues
+    w, v = np.linalg.eigh(J)
+    assert np.allclose(PJ, (v * pf.value(w)) @ v.conj().T, atol=1e-10 * np.abs(PJ).max())
+
+
+def _fd_check(U, action_of_U, F, links, h=1e-5, rtol=1e-9):
+    ULD = U.astype(LD)
+    T = su3.generators(LD)
+    scale = np.sqrt(np.mean(F.astype(np.float64) ** 2))
+    for (t, z, y, x, mu, a) in links:
+        vals = []
+        for s in (+1, -1):
+            V = ULD.copy()
+            R = su3.expm(1j * LD(s * h) * T[a])
+            V[t, z, y, x, mu] = R @ V[t, z, y, x, mu]
+            vals.append(action_of_U(V))
+        fd = np.real(vals[0] - vals[1]) / (2 * LD(h))
+        f = F[t, z, y, x, mu, a]
+        assert abs(float(fd) - float(f)) <= rtol * max(abs(float(fd)), scale), \
+            (t, z, y, x, mu, a, float(fd), float(f))
+
+
+def _links(dims, n, seed):
+    rng = np.random.default_rng(seed)
+    lt = dims[3]
+    out = [(lt - 1, 0, 1, 0, 3, 2), (lt - 1, 1, 0, 1, 3, 7), (0, 1, 1, 0, 0, 0)]
+    for _ in range(n):
+        out.append((int(rng.integers(dims[3])), int(rng.integers(dims[2])),
+                    int(rng.integers(dims[1])), int(rng.integers(dims[0])),
+                    int(rng.integers(4)), int(rng.integers(8))))
+    return out
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_fermion_force_finite_difference(i):
+    dims = (2, 2, 2, 4)
+    U = synthetic.gauge_field(dims, 0.5, 61)
+    chi = lattice.mask(synthetic.spinor_field(dims, 62), dims, 0)
+    t = _terms(0.125, 0.11)[i]
+    F = force.fermion_force(U.astype(LD), t, chi.astype(LD), tol=1e-18)
+    act = lambda V: actions.action(V, t, chi.astype(LD), tol=1e-18)[0]
+    _fd_check(U, act, F, _links(dims, 4, i))
+
+
+def test_plain_force_finite_difference_4444():
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge_field(dims, 0.5, 71)
+    chi = lattice.mask(synthetic.spinor_field(dims, 72), dims, 0)
+    t = actions.term("plain", 0.12)
+    F = force.fermion_force(U.astype(LD), t, chi.astype(LD), tol=1e-18)
+    act = lambda V: actions.action(V, t, chi.astype(LD), tol=1e-18)[0]
+    _fd_check(U, act, F, _links(dims, 2, 5))
+
+
+def test_gauge_force_finite_difference():
+    dims = (2, 2, 4, 4)
+    U = synthetic.gauge_field(dims, 0.7, 81)
+    F = force.gauge_force(U.astype(LD), 5.6)
+    _fd_check(U, lambda V: force.gauge_action(V, 5.6), F, _links(dims, 6, 9))
+
+
+def test_gauge_action_closed_form():
+    """U = 1 gives S_G = 0.  x-links U_x = exp(i th y D), D = diag(1,-1,0), others 1:
+    (x,y) plaquettes are exp(-i th D) except the wrapped row, which carries
+    exp(i th (Ly-1) D); every other plane is trivial."""
+    dims = (2, 4, 2, 2)
+    U = np.zeros(lattice.shape(dims) + (4, 3, 3), dtype=np.complex128)
+    U[...] = np.eye(3)
+    assert abs(force.gauge_action(U, 5.6)) < 1e-12
+    th, ly = 0.3, dims[1]
+    d = np.array([1.0, -1.0, 0.0])
+    for y in range(ly):
+        U[:, :, y, :, 0] = np.diag(np.exp(1j * th * y * d))
+    vol = int(np.prod(dims))
+    per = lambda a: (2.0 / 3.0) * (1 - np.cos(a))
+    closed = 5.6 * vol / ly * ((ly - 1) * per(th) + per((ly - 1) * th))
+    assert abs(force.gauge_action(U, 5.6) - closed) < 1e-12 * closed
