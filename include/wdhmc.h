@@ -1,0 +1,248 @@
+/*
+ * wdhmc.h -- C ABI of the GB300 Wilson-fermion PF/Hasenbusch HMC hot path.
+ *
+ * The method (Haar, Kamleh, Zanotti, Nakamura, "Improving polynomial-filtered
+ * Hybrid Monte Carlo with Hasenbusch", INPC 2016):
+ *   Section 2   lattice action S = S_G + S_F; momenta P with
+ *               H = sum tr P^2 + S; steps T[eps]: U -> exp(i eps P) U and
+ *               S[eps]: P -> P - eps F; Metropolis test; two-flavour fermion
+ *               action S_F = phi^dag (M^dag M)^-1 phi and its force; mass
+ *               preconditioning (Hasenbusch) and polynomial filtering.
+ *   Section 3   Wilson fermions with hopping parameter kappa and even-odd
+ *               preconditioning; cost in multiplications by K (N_mat);
+ *               leapfrog, nested and generalised multi-scale integrators.
+ *   Section 4   PF-MP and three-filter actions.
+ *
+ * Conventions for every call
+ *   - Every pointer to field data is DEVICE memory owned by the caller unless
+ *     the comment says "host".  The library never frees caller memory.
+ *   - The library allocates device memory only in wd_context_create (its
+ *     workspaces and the gauge field copies).
+ *   - Work is ordered on the stream given to wd_context_create.  Calls that
+ *     return a scalar to a host pointer synchronise that stream.
+ *   - Return value: WD_OK or an error code; wd_last_error() gives a message.
+ *     Arguments are validated before any launch; no error aborts the process.
+ *
+ * Lattice: dims[4] = {Lx, Ly, Lz, Lt}, every extent even and >= 2.  Site
+ * (x,y,z,t) has parity (x+y+z+t) mod 2 and checkerboard index
+ * cb = (x + Lx (y + Ly (z + Lz t))) / 2 in [0, Vh), Vh = V/2.  Fermions are
+ * periodic in space and antiperiodic in time; links periodic.  Wilson r = 1,
+ * M = 1 - kappa D, D = sum_mu [(1-g_mu) U_mu(x) psi(x+mu)
+ * + (1+g_mu) U_mu(x-mu)^dag psi(x-mu)], DeGrand-Rossi gamma basis.
+ *
+ * Field layouts (all FP64):
+ *   lexicographic spinor  complex128 [Lt][Lz][Ly][Lx][4 spin][3 colour]
+ *   lexicographic gauge   complex128 [Lt][Lz][Ly][Lx][4 mu][3][3]
+ *   lexicographic algebra float64    [Lt][Lz][Ly][Lx][4 mu][8]
+ *   half spinor (EO)      double2 [12][Vh]: component j = 3*spin + colour of
+ *                         the sites of one parity, structure-of-arrays
+ *   algebra field (EO)    double [4 mu][2 parity][8][Vh]: coordinates
+ *                         X_a of X = sum_a X_a T_a, T_a = lambda_a / 2
+ * Momenta and forces are algebra fields; F_a(x,mu) = dS/dw for
+ * U_mu(x) -> exp(i w T_a) U_mu(x).
+ */
+#ifndef WDHMC_H
+#define WDHMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_ctx wd_ctx;
+
+enum wd_status_code {
+  WD_OK = 0,
+  WD_ERR_ARG = 1,      /* invalid argument (null, size, value); nothing launched */
+  WD_ERR_CUDA = 2,     /* a CUDA call failed */
+  WD_ERR_NOCONV = 3,   /* solver reached maxiter before the tolerance */
+  WD_ERR_NAN = 4,      /* non-finite value met in a solver */
+  WD_ERR_STATE = 5     /* call made before the state it needs (e.g. no gauge field) */
+};
+
+/* Arithmetic used inside an operator application or for the bulk of a solve. */
+enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3 };
+
+/* Storage of the low-precision links: 18 reals, or 12 with the third row
+ * rebuilt as (r0 x r1)^* (SU(3)); the antiperiodic sign is never folded in. */
+enum wd_recon { WD_RECON_18 = 0, WD_RECON_12 = 1 };
+
+/* Pseudofermion term kinds (Section 2; Section 4.1):
+ *   PLAIN       S = phi^dag K^-1 phi,          K = K_hat(kappa)
+ *   HASENBUSCH  S = phi^dag M_h K^-1 M_h^dag phi,  M_h = M_hat(kappa_h), kappa_h < kappa
+ *               (the Hermitian reading of the printed phi^dag J K^-1 phi)
+ *   POLY        S = phi^dag P(K) phi
+ *   FILTERED    S = phi^dag [P(K) K]^-1 phi                                 */
+enum wd_term_kind { WD_TERM_PLAIN = 0, WD_TERM_HASENBUSCH = 1, WD_TERM_POLY = 2,
+                    WD_TERM_FILTERED = 3 };
+
+/* Chebyshev filter P of even degree n approximating 1/x on [eps, lam]
+ * (Section 2: "Chebyshev polynomials ... order p").  Reading: the minimax
+ * relative-error polynomial, x P(x) = 1 - T_{n+1}((mu-x)/nu) / T_{n+1}(mu/nu),
+ * mu = (lam+eps)/2, nu = (lam-eps)/2. */
+typedef struct { int n; double eps; double lam; } wd_poly;
+
+typedef struct {
+  int kind;          /* enum wd_term_kind */
+  double kappa;      /* operator K = K_hat(kappa) */
+  double kappa_h;    /* heavy kappa of a HASENBUSCH term */
+  wd_poly poly;      /* POLY / FILTERED */
+} wd_term;
+
+typedef struct {
+  double tol;        /* stop on the FP64 true residual |b - A x| / |b| <= tol */
+  int maxiter;       /* total iterations allowed */
+  int prec;          /* enum wd_prec: arithmetic of the bulk operator */
+  double delta;      /* reliable update when |r| drops by this factor (mixed) */
+  int check_every;   /* iterations queued between host checks (>= 1) */
+} wd_cg_params;
+
+typedef struct {
+  int iters;                 /* CG iterations */
+  int reliable_updates;      /* FP64 residual recomputations (mixed precision) */
+  long long n_mat;           /* K_hat applications, any precision */
+  double true_rel_resid;     /* FP64 |b - A x| / |b| at return */
+} wd_cg_info;
+
+/* ---- context, fields ------------------------------------------------------ */
+
+/* Create a context for one lattice on the current device; stream may be NULL
+ * (legacy default stream) or a cudaStream_t.  Allocates the workspaces. */
+int wd_context_create(const int dims[4], void* stream, wd_ctx** out);
+int wd_context_destroy(wd_ctx* ctx);
+/* Message of the last error on the calling thread (static storage). */
+const char* wd_last_error(void);
+/* Low-precision link storage (enum wd_recon); takes effect at the next load. */
+int wd_set_recon(wd_ctx* ctx, int recon);
+/* Volume helpers: out[0] = V, out[1] = Vh. */
+int wd_volume(const wd_ctx* ctx, long long out[2]);
+
+/* Load the gauge field from a lexicographic FP64 array (device); builds the
+ * FP64 even-odd copy and the FP32 copy used by low-precision operators. */
+int wd_gauge_load(wd_ctx* ctx, const double* U_lex);
+int wd_gauge_store(wd_ctx* ctx, double* U_lex);
+
+/* Lexicographic spinor <-> half spinor of one parity (other parity ignored /
+ * left untouched by unpack). */
+int wd_spinor_pack(wd_ctx* ctx, int parity, const double* lex, double* eo);
+int wd_spinor_unpack(wd_ctx* ctx, int parity, const double* eo, double* lex);
+/* Lexicographic algebra field <-> EO algebra field. */
+int wd_algebra_pack(wd_ctx* ctx, const double* lex, double* eo);
+int wd_algebra_unpack(wd_ctx* ctx, const double* eo, double* lex);
+
+/* ---- operators (Section 3.1: Wilson, even-odd) ------------------------------ */
+
+/* out = D_{out_parity <- 1-out_parity} in (dagger: D^dag), half spinors.
+ * prec selects the arithmetic: inputs are converted, outputs returned in FP64. */
+int wd_hop(wd_ctx* ctx, int out_parity, int dagger, int prec, const double* in, double* out);
+/* out = M_hat in or M_hat^dag in, M_hat = 1 - kappa^2 D_eo D_oe (even sites). */
+int wd_apply(wd_ctx* ctx, double kappa, int dagger, int prec, const double* in, double* out);
+/* out = K_hat in, K_hat = M_hat^dag M_hat; nrhs consecutive half spinors
+ * (stride 24*Vh doubles).  One K_hat per right-hand side counts as N_mat. */
+int mdagm_apply(wd_ctx* ctx, double kappa, int prec, int nrhs, const double* in, double* out);
+
+/* ---- solvers (Section 2: "iterative solvers (e.g. conjugate gradient)") ----- */
+
+/* Solve A x = b on even sites, A = K_hat(kappa), or A = K_hat P(K_hat) when
+ * filt != NULL (filtered term).  x is the initial guess on entry.  Mixed
+ * precision (p->prec != WD_F64) runs the bulk in that precision and
+ * recomputes the residual in FP64 (reliable updates). */
+int cg_solve(wd_ctx* ctx, double kappa, const wd_poly* filt, const double* b, double* x,
+             const wd_cg_params* p, wd_cg_info* info);
+/* out = P(K_hat(kappa)) in by the Chebyshev three-term recurrence (n K_hat). */
+int poly_filter_apply(wd_ctx* ctx, double kappa, const wd_poly* poly, int prec,
+                      const double* in, double* out);
+
+/* ---- actions and forces (Section 2, eq. of the fermion force) --------------- */
+
+/* S of one term for the half spinor phi; *S is HOST memory. */
+int pf_action(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
+              double* S);
+/* phi such that S(phi) = chi^dag chi for a Gaussian half spinor chi. */
+int pf_heatbath(wd_ctx* ctx, const wd_term* term, const double* chi, const wd_cg_params* p,
+                double* phi);
+/* F += coef * dS/dw (algebra field).  Stores only X = A^-1 psi and Y = M_hat X
+ * per term; polynomial intermediates are recomputed from checkpoints. */
+int fermion_force(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
+                  double coef, double* F);
+/* Wilson plaquette action S_G = beta sum (1 - Re tr U_p / 3); *S host. */
+int gauge_action(wd_ctx* ctx, double beta, double* S);
+/* F += coef * dS_G/dw. */
+int gauge_force(wd_ctx* ctx, double beta, int prec, double coef, double* F);
+
+/* ---- HMC steps (Section 2, eqs. for T-hat and S-hat) ------------------------ */
+
+/* U <- exp(i eps P) U on every link, reunitarised, FP64. */
+int step_T(wd_ctx* ctx, const double* P, double eps);
+/* P <- P - eps F. */
+int step_S(wd_ctx* ctx, double* P, const double* F, double eps);
+/* sum tr P^2 = (1/2) sum_a P_a^2, FP64; *out host. */
+int kinetic_energy(wd_ctx* ctx, const double* P, double* out);
+/* Gaussian draws by Philox4x64-10 (key (seed,0), counter (j, stream, 0, 0)):
+ * what = 0: half spinor of parity `parity` with N(0,1) real and imaginary parts
+ *           (lexicographic element order decides the draw);
+ * what = 1: algebra field (momenta), N(0,1) per coordinate. */
+int gaussian_draw(wd_ctx* ctx, int what, int parity, uint64_t seed, uint64_t stream, double* out);
+/* Accept iff u < exp(-dH); host-only, no device work. */
+int metropolis(double dH, double u, int* accept);
+
+/* ---- HMC trajectory ---------------------------------------------------------- */
+
+/* One operation of an integrator: kind 0 = T[eps]; kind 1 = S[eps] for the
+ * terms in group `group` (group -1 = gauge action). */
+typedef struct { int kind; int group; double eps; } wd_op;
+
+typedef struct {
+  int nterms;
+  const wd_term* terms;      /* host array of fermion terms */
+  const int* term_group;     /* host array: integrator group of each term */
+  double beta;               /* gauge action coupling; <= 0 disables S_G */
+  int nops;
+  const wd_op* ops;          /* host array: the integrator */
+  wd_cg_params cg_md;        /* solves inside the molecular dynamics */
+  wd_cg_params cg_acc;       /* solves for the accept/reject actions */
+  int force_prec;            /* arithmetic of force kernels (WD_F64 / WD_F32) */
+  uint64_t seed;             /* Philox key for momenta and pseudofermions */
+  uint64_t traj_index;       /* counter stream: trajectory number */
+} wd_hmc_params;
+
+typedef struct {
+  double H0, H1, dH;
+  double S_gauge0, S_gauge1;
+  int accepted;
+  long long n_mat;           /* K_hat applications in the trajectory */
+  int n_force_evals;
+} wd_hmc_result;
+
+/* Heat bath, momentum draw, integration, accept/reject with uniform u (host).
+ * On rejection the context's gauge field is restored. */
+int hmc_trajectory(wd_ctx* ctx, const wd_hmc_params* p, double u, wd_hmc_result* res);
+
+/* Build integrator schedules on the host (Section 3.2).  kind 0 = leapfrog,
+ * 1 = Omelyan 2MN.  nested: levels[i] = steps of group i per enclosing T,
+ * outermost first (groups -1 = gauge allowed).  Writes up to cap ops; *nops is
+ * the full length (call with cap 0 to size).  Consecutive S steps of one group
+ * are merged. */
+int wd_schedule_nested(int kind, double tau, int nlevels, const int* groups, const int* steps,
+                       wd_op* ops, int cap, int* nops);
+/* Generalised scheme: overlay per-group integrators of nsteps[i] steps each in
+ * time (Section 3.2), ties ordered by group position (ascending before tau/2,
+ * descending after). */
+int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups,
+                            const int* nsteps, wd_op* ops, int cap, int* nops);
+
+/* ---- counters and timing ---------------------------------------------------- */
+
+/* N_mat: K_hat applications since the context was created or reset. */
+int wd_nmat(wd_ctx* ctx, long long* count, int reset);
+/* Sample every n-th launch of the hop kernels with CUDA events on the context
+ * stream (n = 0 disables).  wd_profile_read gives the sampled launches, their
+ * total device time (ms) and the algorithmic bytes of those launches. */
+int wd_profile_enable(wd_ctx* ctx, int every_n);
+int wd_profile_read(wd_ctx* ctx, long long* launches, double* total_ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

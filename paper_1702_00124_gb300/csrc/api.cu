@@ -1,0 +1,316 @@
+// C ABI: context, error reporting, workspace pool, field layout and operator
+// entry points.  Every entry validates its arguments before any launch.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dslash_impl.cuh"
+
+namespace wd {
+
+static thread_local std::string g_err = "no error";
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(WD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ws_get(wd_ctx* c, int fmt, Field* f) {
+  for (size_t i = 0; i < c->pool.size(); ++i) {
+    if (!c->pool_used[i] && c->pool[i].fmt == fmt) {
+      c->pool_used[i] = true;
+      *f = c->pool[i];
+      return WD_OK;
+    }
+  }
+  Field n;
+  n.fmt = fmt;
+  n.stride = c->g.Vh;
+  WD_CUDA(cudaMalloc(&n.data, field_bytes(fmt, c->g.Vh)));
+  if (fmt == WD_F16 || fmt == WD_BF16) {
+    cudaError_t e = cudaMalloc(&n.norm, sizeof(float) * c->g.Vh);
+    if (e != cudaSuccess) {
+      cudaFree(n.data);
+      return cuda_fail(e, "cudaMalloc(norm)");
+    }
+  }
+  c->pool.push_back(n);
+  c->pool_used.push_back(true);
+  *f = n;
+  return WD_OK;
+}
+
+void ws_put(wd_ctx* c, const Field& f) {
+  for (size_t i = 0; i < c->pool.size(); ++i)
+    if (c->pool[i].data == f.data) c->pool_used[i] = false;
+}
+
+Field wrap_f64(wd_ctx* c, const double* p) {
+  Field f;
+  f.data = const_cast<double*>(p);
+  f.fmt = WD_F64;
+  f.stride = c->g.Vh;
+  return f;
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+#define CHECK_CTX(c) \
+  if ((c) == nullptr) return fail(WD_ERR_ARG, "null context")
+#define CHECK_PTR(p) \
+  if ((p) == nullptr) return fail(WD_ERR_ARG, #p " is null")
+
+static int check_prec(int prec) {
+  if (prec < WD_F64 || prec > WD_BF16) return fail(WD_ERR_ARG, "unknown precision");
+  return WD_OK;
+}
+
+extern "C" {
+
+const char* wd_last_error(void) { return g_err.c_str(); }
+
+int wd_context_create(const int dims[4], void* stream, wd_ctx** out) {
+  CHECK_PTR(dims);
+  CHECK_PTR(out);
+  *out = nullptr;
+  for (int m = 0; m < 4; ++m)
+    if (dims[m] < 2 || dims[m] % 2 != 0) return fail(WD_ERR_ARG, "every lattice extent must be even and >= 2");
+  wd_ctx* c = new (std::nothrow) wd_ctx();
+  if (!c) return fail(WD_ERR_ARG, "out of host memory");
+  for (int m = 0; m < 4; ++m) c->g.L[m] = dims[m];
+  c->g.Lh = dims[0] / 2;
+  c->g.V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+  c->g.Vh = c->g.V / 2;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  const long Vh = c->g.Vh;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t n) { if (e == cudaSuccess) e = cudaMalloc(p, n); };
+  al((void**)&c->gauge64, sizeof(double2) * 72 * Vh);
+  al((void**)&c->gauge32, sizeof(float2) * 72 * Vh);
+  al((void**)&c->gauge32r12, sizeof(float4) * 24 * Vh);
+  al((void**)&c->red_partial, sizeof(double) * 4 * RED_MAX_BLOCKS);
+  al((void**)&c->red_counter, sizeof(unsigned) * 4);
+  al((void**)&c->red_out, sizeof(double) * 16);
+  al((void**)&c->cgs, sizeof(CGState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->cgs_host, sizeof(CGState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_scalar, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, sizeof(unsigned) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->cgs, 0, sizeof(CGState));
+  if (e != cudaSuccess) {
+    std::string m = std::string("wd_context_create: ") + cudaGetErrorString(e);
+    wd_context_destroy(c);
+    return fail(WD_ERR_CUDA, m);
+  }
+  *out = c;
+  return WD_OK;
+}
+
+int wd_context_destroy(wd_ctx* c) {
+  if (!c) return WD_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(c->gauge64);
+  cudaFree(c->gauge32);
+  cudaFree(c->gauge32r12);
+  cudaFree(c->red_partial);
+  cudaFree(c->red_counter);
+  cudaFree(c->red_out);
+  cudaFree(c->cgs);
+  cudaFree(c->gauge_backup);
+  cudaFree(c->mom);
+  if (c->cgs_host) cudaFreeHost(c->cgs_host);
+  if (c->host_scalar) cudaFreeHost(c->host_scalar);
+  for (auto& f : c->pool) {
+    cudaFree(f.data);
+    if (f.norm) cudaFree(f.norm);
+  }
+  for (auto& e : c->prof.ev) cudaEventDestroy(e);
+  delete c;
+  return WD_OK;
+}
+
+int wd_set_recon(wd_ctx* c, int recon) {
+  CHECK_CTX(c);
+  if (recon != WD_RECON_18 && recon != WD_RECON_12) return fail(WD_ERR_ARG, "recon must be 18 or 12");
+  c->recon = recon;
+  return WD_OK;
+}
+
+int wd_volume(const wd_ctx* c, long long out[2]) {
+  CHECK_CTX(c);
+  CHECK_PTR(out);
+  out[0] = c->g.V;
+  out[1] = c->g.Vh;
+  return WD_OK;
+}
+
+int wd_gauge_load(wd_ctx* c, const double* U_lex) {
+  CHECK_CTX(c);
+  CHECK_PTR(U_lex);
+  WD_TRY(pack_k(c, false, 4, 9, 2, -1, U_lex, (double*)c->gauge64));
+  WD_TRY(gauge_lowprec_k(c));
+  c->have_gauge = true;
+  return WD_OK;
+}
+
+int wd_gauge_store(wd_ctx* c, double* U_lex) {
+  CHECK_CTX(c);
+  CHECK_PTR(U_lex);
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return pack_k(c, true, 4, 9, 2, -1, (const double*)c->gauge64, U_lex);
+}
+
+int wd_spinor_pack(wd_ctx* c, int parity, const double* lex, double* eo) {
+  CHECK_CTX(c);
+  CHECK_PTR(lex);
+  CHECK_PTR(eo);
+  if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+  return pack_k(c, false, 1, 12, 2, parity, lex, eo);
+}
+
+int wd_spinor_unpack(wd_ctx* c, int parity, const double* eo, double* lex) {
+  CHECK_CTX(c);
+  CHECK_PTR(lex);
+  CHECK_PTR(eo);
+  if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+  return pack_k(c, true, 1, 12, 2, parity, eo, lex);
+}
+
+int wd_algebra_pack(wd_ctx* c, const double* lex, double* eo) {
+  CHECK_CTX(c);
+  CHECK_PTR(lex);
+  CHECK_PTR(eo);
+  return pack_k(c, false, 4, 8, 1, -1, lex, eo);
+}
+
+int wd_algebra_unpack(wd_ctx* c, const double* eo, double* lex) {
+  CHECK_CTX(c);
+  CHECK_PTR(lex);
+  CHECK_PTR(eo);
+  return pack_k(c, true, 4, 8, 1, -1, eo, lex);
+}
+
+int wd_hop(wd_ctx* c, int out_parity, int dagger, int prec, const double* in, double* out) {
+  CHECK_CTX(c);
+  CHECK_PTR(in);
+  CHECK_PTR(out);
+  WD_TRY(check_prec(prec));
+  if (out_parity != 0 && out_parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  Field fi = wrap_f64(c, in), fo = wrap_f64(c, out);
+  if (prec == WD_F64) return hop(c, out_parity, dagger != 0, fi, fo, nullptr, 0.0, false, false);
+  WsGuard w(c);
+  Field a, b;
+  WD_TRY(w.get(prec, &a));
+  WD_TRY(w.get(prec, &b));
+  WD_TRY(convert(c, fi, a));
+  WD_TRY(hop(c, out_parity, dagger != 0, a, b, nullptr, 0.0, false, false));
+  return convert(c, b, fo);
+}
+
+int wd_apply(wd_ctx* c, double kappa, int dagger, int prec, const double* in, double* out) {
+  CHECK_CTX(c);
+  CHECK_PTR(in);
+  CHECK_PTR(out);
+  WD_TRY(check_prec(prec));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  Field fi = wrap_f64(c, in), fo = wrap_f64(c, out);
+  WsGuard w(c);
+  Field t, a, b;
+  WD_TRY(w.get(prec, &t));
+  if (prec == WD_F64) return apply_mhat(c, kappa, dagger != 0, fi, fo, t, false);
+  WD_TRY(w.get(prec, &a));
+  WD_TRY(w.get(prec, &b));
+  WD_TRY(convert(c, fi, a));
+  WD_TRY(apply_mhat(c, kappa, dagger != 0, a, b, t, false));
+  return convert(c, b, fo);
+}
+
+int mdagm_apply(wd_ctx* c, double kappa, int prec, int nrhs, const double* in, double* out) {
+  CHECK_CTX(c);
+  CHECK_PTR(in);
+  CHECK_PTR(out);
+  WD_TRY(check_prec(prec));
+  if (nrhs < 1) return fail(WD_ERR_ARG, "nrhs must be >= 1");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  WsGuard w(c);
+  Field t1, t2, a, b;
+  WD_TRY(w.get(prec, &t1));
+  WD_TRY(w.get(prec, &t2));
+  if (prec != WD_F64) {
+    WD_TRY(w.get(prec, &a));
+    WD_TRY(w.get(prec == WD_F64 ? WD_F64 : (prec == WD_F32 ? WD_F32 : WD_F32), &b));
+  }
+  const long stride = 24 * c->g.Vh;
+  for (int k = 0; k < nrhs; ++k) {
+    Field fi = wrap_f64(c, in + k * stride), fo = wrap_f64(c, out + k * stride);
+    if (prec == WD_F64) {
+      WD_TRY(apply_khat(c, kappa, fi, fo, t1, t2, false, false));
+    } else {
+      WD_TRY(convert(c, fi, a));
+      WD_TRY(apply_khat(c, kappa, a, b, t1, t2, false, false));
+      WD_TRY(convert(c, b, fo));
+    }
+  }
+  return WD_OK;
+}
+
+int wd_nmat(wd_ctx* c, long long* count, int reset) {
+  CHECK_CTX(c);
+  if (count) *count = c->nmat;
+  if (reset) c->nmat = 0;
+  return WD_OK;
+}
+
+int wd_profile_enable(wd_ctx* c, int every_n) {
+  CHECK_CTX(c);
+  if (every_n < 0) return fail(WD_ERR_ARG, "every_n must be >= 0");
+  c->prof.every = every_n;
+  c->prof.seen = 0;
+  c->prof.launches = 0;
+  c->prof.ms = 0.0;
+  c->prof.bytes = 0.0;
+  for (auto& e : c->prof.ev) cudaEventDestroy(e);
+  c->prof.ev.clear();
+  c->prof.ev_bytes.clear();
+  return WD_OK;
+}
+
+int wd_profile_read(wd_ctx* c, long long* launches, double* total_ms, double* bytes) {
+  CHECK_CTX(c);
+  Prof& p = c->prof;
+  for (size_t k = 0; k + 1 < p.ev.size(); k += 2) {
+    float ms = 0.f;
+    WD_CUDA(cudaEventSynchronize(p.ev[k + 1]));
+    WD_CUDA(cudaEventElapsedTime(&ms, p.ev[k], p.ev[k + 1]));
+    p.ms += ms;
+    p.bytes += p.ev_bytes[k / 2];
+    p.launches += 1;
+    cudaEventDestroy(p.ev[k]);
+    cudaEventDestroy(p.ev[k + 1]);
+  }
+  p.ev.clear();
+  p.ev_bytes.clear();
+  if (launches) *launches = p.launches;
+  if (total_ms) *total_ms = p.ms;
+  if (bytes) *bytes = p.bytes;
+  return WD_OK;
+}
+
+int metropolis(double dH, double u, int* accept) {
+  CHECK_PTR(accept);
+  if (!(u >= 0.0 && u < 1.0)) return fail(WD_ERR_ARG, "u must be in [0, 1)");
+  if (std::isnan(dH)) return fail(WD_ERR_NAN, "dH is NaN");
+  *accept = (u < std::exp(-dH)) ? 1 : 0;
+  return WD_OK;
+}
+
+}  // extern "C"

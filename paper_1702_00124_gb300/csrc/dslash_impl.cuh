@@ -1,0 +1,205 @@
+// Wilson hopping stencil (Section 3.1 of the paper: Wilson fermions, even-odd
+// preconditioning).  One thread per output site of one parity:
+//   (D psi)(x) = sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+// (dagger: the signs of the two projectors swap), fermion sign -1 across the
+// time boundary.  The spin projector reduces each neighbour to a half spinor
+// (2 x 3 complex) before the SU(3) multiply, and the lower half of the result
+// is rebuilt from the upper half.  Optional epilogue: out = y + alpha * D psi,
+// with the FP64 grid sum of |out|^2 (pAp = |M_hat p|^2 for CG).
+#pragma once
+#include "wd_internal.cuh"
+
+namespace wd {
+
+constexpr int HOP_THREADS = 128;
+
+template <int MU, int SG, class T>
+__device__ __forceinline__ void spin_project(const cpx<T> (&s)[12], cpx<T> (&h)[6]) {
+  using Gm = Gam<MU>;
+  constexpr int k0 = Gm::k0 + (SG > 0 ? 0 : 2);
+  constexpr int k1 = Gm::k1 + (SG > 0 ? 0 : 2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h[c] = s[c] + ipow<k0>(s[3 * Gm::p0 + c]);
+    h[3 + c] = s[3 + c] + ipow<k1>(s[3 * Gm::p1 + c]);
+  }
+}
+
+template <int MU, int SG, class T>
+__device__ __forceinline__ void spin_accum(cpx<T> (&acc)[12], const cpx<T> (&u)[6]) {
+  using Gm = Gam<MU>;
+  constexpr int q0 = (SG > 0 ? 0 : 2) - Gm::k0;
+  constexpr int q1 = (SG > 0 ? 0 : 2) - Gm::k1;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + u[c];
+    acc[3 + c] = acc[3 + c] + u[3 + c];
+    acc[3 * Gm::p0 + c] = acc[3 * Gm::p0 + c] + ipow<q0>(u[c]);
+    acc[3 * Gm::p1 + c] = acc[3 * Gm::p1 + c] + ipow<q1>(u[3 + c]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void su3_mul(const cpx<T> (&U)[9], const cpx<T> (&h)[6], cpx<T> (&o)[6]) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      o[3 * a + c] = U[3 * c] * h[3 * a] + U[3 * c + 1] * h[3 * a + 1] + U[3 * c + 2] * h[3 * a + 2];
+}
+
+template <class T>
+__device__ __forceinline__ void su3_dag_mul(const cpx<T> (&U)[9], const cpx<T> (&h)[6], cpx<T> (&o)[6]) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      o[3 * a + c] = cmulc(U[c], h[3 * a]) + cmulc(U[3 + c], h[3 * a + 1]) + cmulc(U[6 + c], h[3 * a + 2]);
+}
+
+template <class In, class Out, class Y, class G>
+struct HopArgs {
+  Geom g;
+  int out_par;
+  In in;
+  Out out;
+  Y y;
+  G gauge;
+  double alpha;
+  Reduce red;
+  CGState* st;
+};
+
+template <int MU, bool DAG, class T, class In, class G>
+__device__ __forceinline__ void hop_dir(const Geom& g, int par, long cb, const int (&c)[4], const In& in,
+                                        const G& gauge, cpx<T> (&acc)[12]) {
+  constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF g_mu
+  constexpr int SB = -SF;             // backward projector
+  // forward neighbour x + mu
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    n[MU] = (n[MU] + 1 == g.L[MU]) ? 0 : n[MU] + 1;
+    const long nb = g.cb_of(n[0], n[1], n[2], n[3]);
+    cpx<T> s[12], h[6], u[6], U[9];
+    in.loadT(nb, s);
+    gauge.load(MU, par, cb, U);
+    spin_project<MU, SF>(s, h);
+    if (MU == 3 && c[3] == g.L[3] - 1) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) h[j] = mk<T>(-h[j].r, -h[j].i);
+    }
+    su3_mul(U, h, u);
+    spin_accum<MU, SF>(acc, u);
+  }
+  // backward neighbour x - mu, link U_mu(x - mu)^dag
+  {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    n[MU] = (n[MU] == 0) ? g.L[MU] - 1 : n[MU] - 1;
+    const long nb = g.cb_of(n[0], n[1], n[2], n[3]);
+    cpx<T> s[12], h[6], u[6], U[9];
+    in.loadT(nb, s);
+    gauge.load(MU, 1 - par, nb, U);
+    spin_project<MU, SB>(s, h);
+    if (MU == 3 && c[3] == 0) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) h[j] = mk<T>(-h[j].r, -h[j].i);
+    }
+    su3_dag_mul(U, h, u);
+    spin_accum<MU, SB>(acc, u);
+  }
+}
+
+template <class T, bool DAG, bool XPAY, bool NORM, class In, class Out, class Y, class G>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop(HopArgs<In, Out, Y, G> a) {
+  if (a.st != nullptr && a.st->flag != 0) return;
+  const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (cb < a.g.Vh) {
+    int c[4];
+    a.g.coords(cb, a.out_par, c);
+    cpx<T> acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = mk<T>(0, 0);
+    hop_dir<0, DAG>(a.g, a.out_par, cb, c, a.in, a.gauge, acc);
+    hop_dir<1, DAG>(a.g, a.out_par, cb, c, a.in, a.gauge, acc);
+    hop_dir<2, DAG>(a.g, a.out_par, cb, c, a.in, a.gauge, acc);
+    hop_dir<3, DAG>(a.g, a.out_par, cb, c, a.in, a.gauge, acc);
+    if constexpr (XPAY) {
+      cpx<T> yv[12];
+      a.y.loadT(cb, yv);
+      const T al = (T)a.alpha;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
+    }
+    if constexpr (NORM) {
+#pragma unroll
+      for (int j = 0; j < 12; ++j) part[0] += (double)acc[j].r * acc[j].r + (double)acc[j].i * acc[j].i;
+    }
+    a.out.store(cb, acc);
+  }
+  if constexpr (NORM) {
+    double tot[1];
+    if (grid_sum<1>(a.red, part, tot)) {
+      CGState* s = a.st;
+      if (s != nullptr) {
+        s->pAp = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0])) s->flag |= FLAG_NAN;
+        else s->alpha = s->rr / tot[0];
+      }
+    }
+  }
+}
+
+template <class T, class In, class Out, class Y, class G>
+int launch_hop(wd_ctx* c, bool dag, bool xpay, bool norm, const HopArgs<In, Out, Y, G>& a) {
+  const int nb = nblocks(c->g.Vh, HOP_THREADS);
+  if (norm && nb > RED_MAX_BLOCKS) return fail(WD_ERR_ARG, "lattice too large for one reduction grid");
+#define WD_L(D, X, N) k_hop<T, D, X, N, In, Out, Y, G><<<nb, HOP_THREADS, 0, c->stream>>>(a)
+  if (!dag) {
+    if (!xpay) WD_L(false, false, false);
+    else if (!norm) WD_L(false, true, false);
+    else WD_L(false, true, true);
+  } else {
+    if (!xpay) WD_L(true, false, false);
+    else if (!norm) WD_L(true, true, false);
+    else WD_L(true, true, true);
+  }
+#undef WD_L
+  WD_CHECK_LAUNCH();
+  return WD_OK;
+}
+
+// format objects from fields
+inline SpF64 sp64(const Field& f) { return SpF64{(double2*)f.data, f.stride}; }
+inline SpF32 sp32(const Field& f) { return SpF32{(float4*)f.data, f.stride}; }
+template <class H> inline Sp16<H> sp16(const Field& f) { return Sp16<H>{(uint4*)f.data, f.norm, f.stride}; }
+
+template <class T, class In, class Out, class Y>
+int hop_with_gauge(wd_ctx* c, int out_par, bool dag, In in, Out out, Y y, bool xpay, double alpha,
+                   bool norm_cg, bool in_cg, bool use64) {
+  Reduce red = reducer(c);
+  CGState* st = (norm_cg || in_cg) ? c->cgs : nullptr;
+  if (use64) {
+    GF64 G{c->gauge64, c->g.Vh};
+    HopArgs<In, Out, Y, GF64> a{c->g, out_par, in, out, y, G, alpha, red, st};
+    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+  }
+  if (c->recon == WD_RECON_12) {
+    GF32R12 G{c->gauge32r12, c->g.Vh};
+    HopArgs<In, Out, Y, GF32R12> a{c->g, out_par, in, out, y, G, alpha, red, st};
+    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+  }
+  GF32 G{c->gauge32, c->g.Vh};
+  HopArgs<In, Out, Y, GF32> a{c->g, out_par, in, out, y, G, alpha, red, st};
+  return launch_hop<T>(c, dag, xpay, norm_cg, a);
+}
+
+// per-family dispatchers (one translation unit each)
+int hop_f64(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
+            double alpha, bool norm_cg, bool in_cg);
+int hop_f32(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
+            double alpha, bool norm_cg, bool in_cg);
+int hop_h16(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
+            double alpha, bool norm_cg, bool in_cg);
+
+}  // namespace wd

@@ -1,0 +1,552 @@
+// Pseudofermion terms (actions, heat bath, forces), HMC trajectory and
+// integrator schedules.
+//
+// Terms (Section 2 of the paper; Section 4.1 for PF-MP), each on
+// K = K_hat(kappa) = M_hat^dag M_hat:
+//   PLAIN       S = phi^dag K^-1 phi                 heat bath phi = M^dag chi
+//   HASENBUSCH  S = phi^dag M_h K^-1 M_h^dag phi     phi = M_h J^-1 M^dag chi, J = K_hat(kappa_h)
+//   POLY        S = phi^dag P(K) phi                 phi = P^-1 C^dag chi, P = C^dag C
+//   FILTERED    S = phi^dag [P(K) K]^-1 phi          phi = C^dag M^dag chi
+// with C = sqrt(c) prod_{k <= n/2} (K - z_k).  Actions use the variational
+// estimate S = 2 Re(b^dag X) - X^dag A X of b^dag A^-1 b, whose error is
+// quadratic in the solver residual.
+//
+// Forces: F_a = dS/dw, w the angle of U_mu(x) -> exp(i w T_a) U_mu(x).  With
+// X = A^-1 psi and Y = M_hat X:
+//   PLAIN       F = 2 kappa^2 Re(Y~^dag dD X~)
+//   HASENBUSCH  same with psi = M_h^dag phi, plus -2 kappa_h^2 Re(phi~^dag dD X~)
+//   POLY        S = v^dag Q(K) v, Q = s prod_k (K - r_k):
+//               dS = s sum_k Re(L_k^dag dK R_k), L_k = prod_{j<k} (K - r_j^*) v,
+//               R_k = prod_{j>k} (K - r_j) v
+//   FILTERED    minus the POLY force of Q(x) = x P(x) at v = X
+// where A~ = (A, D^dag_oe A) and B~ = (B, D_oe B) extend even fields to the
+// full lattice.  Only X and Y are kept per PLAIN/HASENBUSCH term; for
+// polynomial terms the vectors R_k are recomputed segment by segment from
+// ceil(sqrt(m)) checkpoints instead of being stored.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "dslash_impl.cuh"
+
+namespace wd {
+
+static int check_term(const wd_term* t) {
+  if (t == nullptr) return fail(WD_ERR_ARG, "term is null");
+  if (t->kind < WD_TERM_PLAIN || t->kind > WD_TERM_FILTERED) return fail(WD_ERR_ARG, "unknown term kind");
+  if (t->kind >= WD_TERM_POLY) {
+    PolyCoef pc;
+    WD_TRY(poly_coef(t->poly, &pc));
+  }
+  return WD_OK;
+}
+
+static int check_cg(const wd_cg_params* p) {
+  if (p == nullptr) return fail(WD_ERR_ARG, "cg params are null");
+  if (!(p->tol > 0) || p->maxiter < 1) return fail(WD_ERR_ARG, "cg params: tol > 0 and maxiter >= 1 required");
+  if (p->prec < WD_F64 || p->prec > WD_BF16) return fail(WD_ERR_ARG, "cg params: unknown precision");
+  return WD_OK;
+}
+
+static int force_fmt(const wd_cg_params& p) { return p.prec == WD_F64 ? WD_F64 : WD_F32; }
+
+// F += coef * d/dw Re(A^dag M_hat B) = coef * (-kappa^2) Re(A~^dag dD B~)
+static int mhat_outer(wd_ctx* c, double kappa, const Field& A, const Field& B, double coef, double* F) {
+  WsGuard w(c);
+  Field Ao, Bo;
+  WD_TRY(w.get(A.fmt, &Ao));
+  WD_TRY(w.get(A.fmt, &Bo));
+  WD_TRY(hop(c, 1, true, A, Ao, nullptr, 0.0, false, false));
+  WD_TRY(hop(c, 1, false, B, Bo, nullptr, 0.0, false, false));
+  return force_outer(c, -coef * kappa * kappa, A, Ao, B, Bo, F, A.fmt);
+}
+
+static int mhat(wd_ctx* c, double kappa, bool dag, const Field& in, const Field& out) {
+  WsGuard w(c);
+  Field t;
+  WD_TRY(w.get(in.fmt, &t));
+  return apply_mhat(c, kappa, dag, in, out, t, false);
+}
+
+// out = K x - z x  (z complex; conj_z selects conj(z))
+static int k_minus(wd_ctx* c, double kappa, double zr, double zi, const Field& x, const Field& out) {
+  WsGuard w(c);
+  Field k;
+  WD_TRY(w.get(x.fmt, &k));
+  WD_TRY(khat_any(c, kappa, x, k));
+  return caxpby(c, 1.0, 0.0, k, -zr, -zi, x, out);
+}
+
+// Force of S = v^dag Q(K) v, Q = scale prod_k (K - r_k), added with coef.
+static int poly_force(wd_ctx* c, double kappa, const std::vector<double>& rr, const std::vector<double>& ri,
+                      double scale, const Field& v, double coef, double* F) {
+  const int m = (int)rr.size();
+  const int f = v.fmt;
+  const int seg = std::max(1, (int)std::ceil(std::sqrt((double)m)));
+  const int nseg = (m + seg - 1) / seg;
+  WsGuard w(c);
+  std::vector<Field> cp(nseg), buf(seg);
+  Field L, Ln, ML, MR, cur;
+  for (auto& x : cp) WD_TRY(w.get(f, &x));
+  for (auto& x : buf) WD_TRY(w.get(f, &x));
+  WD_TRY(w.get(f, &L));
+  WD_TRY(w.get(f, &Ln));
+  WD_TRY(w.get(f, &ML));
+  WD_TRY(w.get(f, &MR));
+  WD_TRY(w.get(f, &cur));
+  auto seg_end = [&](int s) { return std::min((s + 1) * seg, m) - 1; };
+  // backward pass: R_{m-1} = v, R_{k-1} = (K - r_k) R_k; keep R at segment ends
+  WD_TRY(convert(c, v, cur));
+  for (int s = nseg - 1, k = m - 1; k >= 0; --k) {
+    if (s >= 0 && k == seg_end(s)) { WD_TRY(convert(c, cur, cp[s])); --s; }
+    if (k > 0) WD_TRY(k_minus(c, kappa, rr[k], ri[k], cur, cur));
+  }
+  // forward pass over k with L_k; R_k rebuilt from the segment's checkpoint
+  WD_TRY(convert(c, v, L));
+  for (int s = 0; s < nseg; ++s) {
+    const int a = s * seg, b = seg_end(s);
+    WD_TRY(convert(c, cp[s], buf[b - a]));
+    for (int j = b - a; j >= 1; --j) WD_TRY(k_minus(c, kappa, rr[a + j], ri[a + j], buf[j], buf[j - 1]));
+    for (int k = a; k <= b; ++k) {
+      const Field& R = buf[k - a];
+      WD_TRY(mhat(c, kappa, false, R, MR));
+      WD_TRY(mhat(c, kappa, false, L, ML));
+      WD_TRY(mhat_outer(c, kappa, MR, L, coef * scale, F));
+      WD_TRY(mhat_outer(c, kappa, ML, R, coef * scale, F));
+      if (k < m - 1) {
+        WD_TRY(k_minus(c, kappa, rr[k], -ri[k], L, Ln));
+        std::swap(L, Ln);
+      }
+    }
+  }
+  return WD_OK;
+}
+
+// C^dag v = sqrt(c) prod_{k<=n/2} (K - conj z_k) v
+static int apply_cdag(wd_ctx* c, double kappa, const PolyCoef& pc, const Field& v, const Field& out) {
+  WD_TRY(axpby(c, std::sqrt(pc.scale), v, 0.0, v, out));
+  for (int k = 0; k < pc.n / 2; ++k) WD_TRY(k_minus(c, kappa, pc.zr[k], -pc.zi[k], out, out));
+  return WD_OK;
+}
+
+static int solve(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, const Field& x,
+                 const wd_cg_params& p) {
+  WD_TRY(zero(c, x));
+  wd_cg_info info;
+  return cg_solve_f(c, kappa, filt, b, x, p, &info);
+}
+
+int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double* S) {
+  WsGuard w(c);
+  Field b, X, AX, tmp;
+  WD_TRY(w.get(WD_F64, &b));
+  WD_TRY(w.get(WD_F64, &X));
+  WD_TRY(w.get(WD_F64, &AX));
+  double re, xax;
+  switch (t.kind) {
+    case WD_TERM_PLAIN:
+    case WD_TERM_HASENBUSCH: {
+      if (t.kind == WD_TERM_PLAIN) WD_TRY(convert(c, phi, b));
+      else WD_TRY(mhat(c, t.kappa_h, true, phi, b));
+      WD_TRY(solve(c, t.kappa, nullptr, b, X, p));
+      WD_TRY(mhat(c, t.kappa, false, X, AX));       // |M X|^2 = X^dag K X
+      WD_TRY(dot(c, b, X, &re, nullptr));
+      WD_TRY(norm2(c, AX, &xax));
+      *S = 2.0 * re - xax;
+      return WD_OK;
+    }
+    case WD_TERM_POLY: {
+      WD_TRY(poly_apply_f(c, t.kappa, t.poly, WD_F64, phi, AX));
+      WD_TRY(dot(c, phi, AX, &re, nullptr));
+      *S = re;
+      return WD_OK;
+    }
+    case WD_TERM_FILTERED: {
+      WD_TRY(w.get(WD_F64, &tmp));
+      WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
+      WD_TRY(poly_apply_f(c, t.kappa, t.poly, WD_F64, X, tmp));
+      WD_TRY(khat_any(c, t.kappa, tmp, AX));
+      WD_TRY(dot(c, phi, X, &re, nullptr));
+      WD_TRY(dot(c, X, AX, &xax, nullptr));
+      *S = 2.0 * re - xax;
+      return WD_OK;
+    }
+  }
+  return fail(WD_ERR_ARG, "unknown term kind");
+}
+
+int term_heatbath(wd_ctx* c, const wd_term& t, const Field& chi, const wd_cg_params& p, const Field& phi) {
+  WsGuard w(c);
+  Field y, z;
+  WD_TRY(w.get(WD_F64, &y));
+  switch (t.kind) {
+    case WD_TERM_PLAIN:
+      return mhat(c, t.kappa, true, chi, phi);
+    case WD_TERM_HASENBUSCH:
+      WD_TRY(w.get(WD_F64, &z));
+      WD_TRY(mhat(c, t.kappa, true, chi, y));
+      WD_TRY(solve(c, t.kappa_h, nullptr, y, z, p));
+      return mhat(c, t.kappa_h, false, z, phi);
+    case WD_TERM_POLY: {
+      PolyCoef pc;
+      WD_TRY(poly_coef(t.poly, &pc));
+      WD_TRY(apply_cdag(c, t.kappa, pc, chi, y));
+      WD_TRY(zero(c, phi));
+      wd_cg_info info;
+      return cg_solve_poly(c, t.kappa, t.poly, y, phi, p, &info);
+    }
+    case WD_TERM_FILTERED: {
+      PolyCoef pc;
+      WD_TRY(poly_coef(t.poly, &pc));
+      WD_TRY(mhat(c, t.kappa, true, chi, y));
+      return apply_cdag(c, t.kappa, pc, y, phi);
+    }
+  }
+  return fail(WD_ERR_ARG, "unknown term kind");
+}
+
+int term_force(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double coef, double* F) {
+  const int f = force_fmt(p);
+  WsGuard w(c);
+  Field b, X, Xf, Yf, phif;
+  WD_TRY(w.get(WD_F64, &X));
+  switch (t.kind) {
+    case WD_TERM_PLAIN:
+    case WD_TERM_HASENBUSCH: {
+      WD_TRY(w.get(WD_F64, &b));
+      if (t.kind == WD_TERM_PLAIN) WD_TRY(convert(c, phi, b));
+      else WD_TRY(mhat(c, t.kappa_h, true, phi, b));
+      WD_TRY(solve(c, t.kappa, nullptr, b, X, p));
+      WD_TRY(w.get(f, &Xf));
+      WD_TRY(w.get(f, &Yf));
+      WD_TRY(convert(c, X, Xf));
+      WD_TRY(mhat(c, t.kappa, false, Xf, Yf));
+      WD_TRY(mhat_outer(c, t.kappa, Yf, Xf, -2.0 * coef, F));
+      if (t.kind == WD_TERM_HASENBUSCH) {
+        WD_TRY(w.get(f, &phif));
+        WD_TRY(convert(c, phi, phif));
+        WD_TRY(mhat_outer(c, t.kappa_h, phif, Xf, 2.0 * coef, F));
+      }
+      return WD_OK;
+    }
+    case WD_TERM_POLY: {
+      PolyCoef pc;
+      WD_TRY(poly_coef(t.poly, &pc));
+      WD_TRY(w.get(f, &phif));
+      WD_TRY(convert(c, phi, phif));
+      return poly_force(c, t.kappa, pc.zr, pc.zi, pc.scale, phif, coef, F);
+    }
+    case WD_TERM_FILTERED: {
+      PolyCoef pc;
+      WD_TRY(poly_coef(t.poly, &pc));
+      WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
+      WD_TRY(w.get(f, &Xf));
+      WD_TRY(convert(c, X, Xf));
+      std::vector<double> rr(1, 0.0), ri(1, 0.0);
+      rr.insert(rr.end(), pc.zr.begin(), pc.zr.end());
+      ri.insert(ri.end(), pc.zi.begin(), pc.zi.end());
+      return poly_force(c, t.kappa, rr, ri, pc.scale, Xf, -coef, F);
+    }
+  }
+  return fail(WD_ERR_ARG, "unknown term kind");
+}
+
+// ----------------------------------------------------------------------------
+// schedules (Section 3.2)
+struct OpV {
+  int kind, group;
+  double eps;
+};
+
+static void base_scheme(int kind, int n, double tau, int g, std::vector<OpV>& out) {
+  const double h = tau / n;
+  const double lam = 0.1931833275037836;   // Omelyan, Mryglod, Folk (2003), 2MN
+  for (int i = 0; i < n; ++i) {
+    if (kind == 0) {
+      out.push_back({1, g, h / 2});
+      out.push_back({0, 0, h});
+      out.push_back({1, g, h / 2});
+    } else {
+      out.push_back({1, g, lam * h});
+      out.push_back({0, 0, h / 2});
+      out.push_back({1, g, (1 - 2 * lam) * h});
+      out.push_back({0, 0, h / 2});
+      out.push_back({1, g, lam * h});
+    }
+  }
+}
+
+static void nested_rec(int kind, double tau, int lv, int nl, const int* groups, const int* steps,
+                       std::vector<OpV>& out) {
+  std::vector<OpV> ops;
+  base_scheme(kind, steps[lv], tau, groups[lv], ops);
+  for (auto& o : ops) {
+    if (o.kind == 0 && lv + 1 < nl) nested_rec(kind, o.eps, lv + 1, nl, groups, steps, out);
+    else out.push_back(o);
+  }
+}
+
+// S steps between two T steps commute (each force depends on U only): sum
+// them per group, in order of first appearance.
+static std::vector<OpV> canonical(const std::vector<OpV>& in) {
+  std::vector<OpV> out;
+  std::vector<OpV> run;
+  auto flush = [&]() {
+    for (auto& o : run) out.push_back(o);
+    run.clear();
+  };
+  for (auto& o : in) {
+    if (o.kind == 0) {
+      flush();
+      out.push_back(o);
+    } else {
+      bool merged = false;
+      for (auto& r : run)
+        if (r.group == o.group) { r.eps += o.eps; merged = true; break; }
+      if (!merged) run.push_back(o);
+    }
+  }
+  flush();
+  return out;
+}
+
+static int emit(const std::vector<OpV>& v, wd_op* ops, int cap, int* nops) {
+  if (nops) *nops = (int)v.size();
+  if (ops) for (int i = 0; i < (int)v.size() && i < cap; ++i) ops[i] = wd_op{v[i].kind, v[i].group, v[i].eps};
+  return WD_OK;
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+extern "C" {
+
+int wd_schedule_nested(int kind, double tau, int nlevels, const int* groups, const int* steps, wd_op* ops,
+                       int cap, int* nops) {
+  if (kind != 0 && kind != 1) return fail(WD_ERR_ARG, "kind must be 0 (leapfrog) or 1 (2MN)");
+  if (nlevels < 1 || !groups || !steps || !(tau > 0)) return fail(WD_ERR_ARG, "bad schedule arguments");
+  for (int i = 0; i < nlevels; ++i)
+    if (steps[i] < 1) return fail(WD_ERR_ARG, "steps must be >= 1");
+  std::vector<OpV> v;
+  nested_rec(kind, tau, 0, nlevels, groups, steps, v);
+  return emit(canonical(v), ops, cap, nops);
+}
+
+int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups, const int* nsteps,
+                            wd_op* ops, int cap, int* nops) {
+  if (kind != 0 && kind != 1) return fail(WD_ERR_ARG, "kind must be 0 (leapfrog) or 1 (2MN)");
+  if (ngroups < 1 || !groups || !nsteps || !(tau > 0)) return fail(WD_ERR_ARG, "bad schedule arguments");
+  struct Ev { double t; int pos; OpV op; };
+  std::vector<Ev> ev;
+  for (int i = 0; i < ngroups; ++i) {
+    if (nsteps[i] < 1) return fail(WD_ERR_ARG, "nsteps must be >= 1");
+    std::vector<OpV> s;
+    base_scheme(kind, nsteps[i], tau, groups[i], s);
+    double t = 0;
+    for (auto& o : s) {
+      if (o.kind == 0) t += o.eps;
+      else ev.push_back({t, i, o});
+    }
+  }
+  const double tolt = 1e-12 * tau;
+  std::vector<double> times;
+  for (auto& e : ev) times.push_back(e.t);
+  std::sort(times.begin(), times.end());
+  std::vector<double> uniq;
+  for (double t : times)
+    if (uniq.empty() || t - uniq.back() > tolt) uniq.push_back(t);
+  std::vector<OpV> out;
+  double prev = 0;
+  for (double t : uniq) {
+    if (t - prev > tolt) out.push_back({0, 0, t - prev});
+    std::vector<Ev> here;
+    for (auto& e : ev)
+      if (std::fabs(e.t - t) <= tolt) here.push_back(e);
+    const bool desc = t >= tau / 2 - tolt;
+    std::stable_sort(here.begin(), here.end(),
+                     [&](const Ev& a, const Ev& b) { return desc ? a.pos > b.pos : a.pos < b.pos; });
+    for (auto& e : here) out.push_back(e.op);
+    prev = t;
+  }
+  if (tau - prev > tolt) out.push_back({0, 0, tau - prev});
+  return emit(canonical(out), ops, cap, nops);
+}
+
+int cg_solve(wd_ctx* c, double kappa, const wd_poly* filt, const double* b, double* x,
+             const wd_cg_params* p, wd_cg_info* info) {
+  if (!c) return fail(WD_ERR_ARG, "null context");
+  if (!b || !x) return fail(WD_ERR_ARG, "b and x must be device pointers");
+  WD_TRY(check_cg(p));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  if (filt) {
+    PolyCoef pc;
+    WD_TRY(poly_coef(*filt, &pc));
+  }
+  return cg_solve_f(c, kappa, filt, wrap_f64(c, b), wrap_f64(c, x), *p, info);
+}
+
+int poly_filter_apply(wd_ctx* c, double kappa, const wd_poly* poly, int prec, const double* in, double* out) {
+  if (!c || !poly || !in || !out) return fail(WD_ERR_ARG, "null argument");
+  if (prec != WD_F64 && prec != WD_F32) return fail(WD_ERR_ARG, "poly_filter_apply: FP64 or FP32");
+  if (in == out) return fail(WD_ERR_ARG, "poly_filter_apply: in and out must differ");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  PolyCoef pc;
+  WD_TRY(poly_coef(*poly, &pc));
+  if (prec == WD_F64) return poly_apply_f(c, kappa, *poly, prec, wrap_f64(c, in), wrap_f64(c, out));
+  WsGuard w(c);
+  Field a, b;
+  WD_TRY(w.get(WD_F32, &a));
+  WD_TRY(w.get(WD_F32, &b));
+  WD_TRY(convert(c, wrap_f64(c, in), a));
+  WD_TRY(poly_apply_f(c, kappa, *poly, prec, a, b));
+  return convert(c, b, wrap_f64(c, out));
+}
+
+int pf_action(wd_ctx* c, const wd_term* term, const double* phi, const wd_cg_params* p, double* S) {
+  if (!c || !phi || !S) return fail(WD_ERR_ARG, "null argument");
+  WD_TRY(check_term(term));
+  WD_TRY(check_cg(p));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return term_action(c, *term, wrap_f64(c, phi), *p, S);
+}
+
+int pf_heatbath(wd_ctx* c, const wd_term* term, const double* chi, const wd_cg_params* p, double* phi) {
+  if (!c || !chi || !phi) return fail(WD_ERR_ARG, "null argument");
+  if (chi == phi) return fail(WD_ERR_ARG, "chi and phi must differ");
+  WD_TRY(check_term(term));
+  WD_TRY(check_cg(p));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return term_heatbath(c, *term, wrap_f64(c, chi), *p, wrap_f64(c, phi));
+}
+
+int fermion_force(wd_ctx* c, const wd_term* term, const double* phi, const wd_cg_params* p, double coef,
+                  double* F) {
+  if (!c || !phi || !F) return fail(WD_ERR_ARG, "null argument");
+  WD_TRY(check_term(term));
+  WD_TRY(check_cg(p));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return term_force(c, *term, wrap_f64(c, phi), *p, coef, F);
+}
+
+int gauge_action(wd_ctx* c, double beta, double* S) {
+  if (!c || !S) return fail(WD_ERR_ARG, "null argument");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  double s;
+  WD_TRY(gauge_action_k(c, &s));
+  *S = beta * s;
+  return WD_OK;
+}
+
+int gauge_force(wd_ctx* c, double beta, int prec, double coef, double* F) {
+  if (!c || !F) return fail(WD_ERR_ARG, "null argument");
+  if (prec != WD_F64 && prec != WD_F32) return fail(WD_ERR_ARG, "gauge_force: FP64 or FP32");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return gauge_force_k(c, beta, prec, coef, F);
+}
+
+int step_T(wd_ctx* c, const double* P, double eps) {
+  if (!c || !P) return fail(WD_ERR_ARG, "null argument");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  return step_T_k(c, P, eps);
+}
+
+int step_S(wd_ctx* c, double* P, const double* F, double eps) {
+  if (!c || !P || !F) return fail(WD_ERR_ARG, "null argument");
+  return step_S_k(c, P, F, eps);
+}
+
+int kinetic_energy(wd_ctx* c, const double* P, double* out) {
+  if (!c || !P || !out) return fail(WD_ERR_ARG, "null argument");
+  return kinetic_k(c, P, out);
+}
+
+int gaussian_draw(wd_ctx* c, int what, int parity, uint64_t seed, uint64_t stream, double* out) {
+  if (!c || !out) return fail(WD_ERR_ARG, "null argument");
+  if (what != 0 && what != 1) return fail(WD_ERR_ARG, "what must be 0 (spinor) or 1 (algebra)");
+  if (what == 0 && parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+  return gaussian_draw_k(c, what, parity, seed, stream, out);
+}
+
+int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* res) {
+  if (!c || !p || !res) return fail(WD_ERR_ARG, "null argument");
+  if (p->nterms < 0 || (p->nterms > 0 && (!p->terms || !p->term_group))) return fail(WD_ERR_ARG, "bad terms");
+  if (p->nops < 1 || !p->ops) return fail(WD_ERR_ARG, "empty integrator");
+  if (!(u >= 0.0 && u < 1.0)) return fail(WD_ERR_ARG, "u must be in [0, 1)");
+  for (int i = 0; i < p->nterms; ++i) WD_TRY(check_term(&p->terms[i]));
+  WD_TRY(check_cg(&p->cg_md));
+  WD_TRY(check_cg(&p->cg_acc));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  const long Vh = c->g.Vh;
+  if (!c->gauge_backup) WD_CUDA(cudaMalloc(&c->gauge_backup, sizeof(double2) * 72 * Vh));
+  if (!c->mom) WD_CUDA(cudaMalloc(&c->mom, sizeof(double) * 64 * Vh));
+  WD_CUDA(cudaMemcpyAsync(c->gauge_backup, c->gauge64, sizeof(double2) * 72 * Vh, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  const long long nmat0 = c->nmat;
+  const uint64_t base = p->traj_index * 64;
+  wd_cg_params md = p->cg_md;
+  md.prec = p->force_prec == WD_F64 ? WD_F64 : p->cg_md.prec;
+  WsGuard w(c);
+  std::vector<Field> phi(p->nterms);
+  Field chi;
+  WD_TRY(w.get(WD_F64, &chi));
+  for (auto& f : phi) WD_TRY(w.get(WD_F64, &f));
+  // momenta and pseudofermions
+  WD_TRY(gaussian_draw_k(c, 1, 0, p->seed, base, c->mom));
+  for (int i = 0; i < p->nterms; ++i) {
+    WD_TRY(gaussian_draw_k(c, 0, 0, p->seed, base + 1 + i, (double*)chi.data));
+    WD_TRY(term_heatbath(c, p->terms[i], chi, p->cg_acc, phi[i]));
+  }
+  auto hamiltonian = [&](double* H, double* SG) -> int {
+    double k, s, sum;
+    WD_TRY(kinetic_k(c, c->mom, &k));
+    sum = k;
+    *SG = 0;
+    if (p->beta > 0) {
+      WD_TRY(gauge_action_k(c, &s));
+      *SG = p->beta * s;
+      sum += *SG;
+    }
+    for (int i = 0; i < p->nterms; ++i) {
+      WD_TRY(term_action(c, p->terms[i], phi[i], p->cg_acc, &s));
+      sum += s;
+    }
+    *H = sum;
+    return WD_OK;
+  };
+  WD_TRY(hamiltonian(&res->H0, &res->S_gauge0));
+  int nf = 0;
+  const int fprec = p->force_prec == WD_F64 ? WD_F64 : WD_F32;
+  for (int k = 0; k < p->nops; ++k) {
+    const wd_op& o = p->ops[k];
+    if (o.kind == 0) {
+      WD_TRY(step_T_k(c, c->mom, o.eps));
+    } else {
+      if (o.group == -1 && p->beta > 0) {
+        WD_TRY(gauge_force_k(c, p->beta, fprec, -o.eps, c->mom));
+        ++nf;
+      }
+      for (int i = 0; i < p->nterms; ++i) {
+        if (p->term_group[i] != o.group) continue;
+        WD_TRY(term_force(c, p->terms[i], phi[i], md, -o.eps, c->mom));
+        ++nf;
+      }
+    }
+  }
+  WD_TRY(hamiltonian(&res->H1, &res->S_gauge1));
+  res->dH = res->H1 - res->H0;
+  res->n_force_evals = nf;
+  int acc = 0;
+  WD_TRY(metropolis(res->dH, u, &acc));
+  res->accepted = acc;
+  if (!acc) {
+    WD_CUDA(cudaMemcpyAsync(c->gauge64, c->gauge_backup, sizeof(double2) * 72 * Vh, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    WD_TRY(gauge_lowprec_k(c));
+  }
+  res->n_mat = c->nmat - nmat0;
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return WD_OK;
+}
+
+}  // extern "C"

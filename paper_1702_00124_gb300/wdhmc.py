@@ -1,0 +1,304 @@
+"""Thin Python binding of libwdhmc (include/wdhmc.h).
+
+Argument marshalling only: every function forwards torch tensors' device
+pointers to the C entry point of the same name and raises on a non-zero
+status.  All computation happens in the CUDA library; there is no fallback:
+importing this module without the built library raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libwdhmc.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libwdhmc.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+lib = C.CDLL(_LIB_PATH)
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+RECON_18, RECON_12 = 0, 1
+PLAIN, HASENBUSCH, POLY, FILTERED = 0, 1, 2, 3
+ERRORS = {1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_NOCONV", 4: "WD_ERR_NAN", 5: "WD_ERR_STATE"}
+
+
+class WdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class wd_poly(C.Structure):
+    _fields_ = [("n", C.c_int), ("eps", C.c_double), ("lam", C.c_double)]
+
+
+class wd_term(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("kappa_h", C.c_double), ("poly", wd_poly)]
+
+
+class wd_cg_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("prec", C.c_int), ("delta", C.c_double),
+                ("check_every", C.c_int)]
+
+
+class wd_cg_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("n_mat", C.c_longlong),
+                ("true_rel_resid", C.c_double)]
+
+
+class wd_op(C.Structure):
+    _fields_ = [("kind", C.c_int), ("group", C.c_int), ("eps", C.c_double)]
+
+
+class wd_hmc_params(C.Structure):
+    _fields_ = [("nterms", C.c_int), ("terms", C.POINTER(wd_term)), ("term_group", C.POINTER(C.c_int)),
+                ("beta", C.c_double), ("nops", C.c_int), ("ops", C.POINTER(wd_op)),
+                ("cg_md", wd_cg_params), ("cg_acc", wd_cg_params), ("force_prec", C.c_int),
+                ("seed", C.c_uint64), ("traj_index", C.c_uint64)]
+
+
+class wd_hmc_result(C.Structure):
+    _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("dH", C.c_double), ("S_gauge0", C.c_double),
+                ("S_gauge1", C.c_double), ("accepted", C.c_int), ("n_mat", C.c_longlong),
+                ("n_force_evals", C.c_int)]
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+_SIG = {
+    "wd_last_error": ([], C.c_char_p),
+    "wd_context_create": ([C.POINTER(C.c_int), _P, C.POINTER(_P)], _I),
+    "wd_context_destroy": ([_P], _I),
+    "wd_set_recon": ([_P, _I], _I),
+    "wd_volume": ([_P, C.POINTER(C.c_longlong)], _I),
+    "wd_gauge_load": ([_P, _P], _I),
+    "wd_gauge_store": ([_P, _P], _I),
+    "wd_spinor_pack": ([_P, _I, _P, _P], _I),
+    "wd_spinor_unpack": ([_P, _I, _P, _P], _I),
+    "wd_algebra_pack": ([_P, _P, _P], _I),
+    "wd_algebra_unpack": ([_P, _P, _P], _I),
+    "wd_hop": ([_P, _I, _I, _I, _P, _P], _I),
+    "wd_apply": ([_P, _D, _I, _I, _P, _P], _I),
+    "mdagm_apply": ([_P, _D, _I, _I, _P, _P], _I),
+    "cg_solve": ([_P, _D, C.POINTER(wd_poly), _P, _P, C.POINTER(wd_cg_params), C.POINTER(wd_cg_info)], _I),
+    "poly_filter_apply": ([_P, _D, C.POINTER(wd_poly), _I, _P, _P], _I),
+    "pf_action": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), C.POINTER(_D)], _I),
+    "pf_heatbath": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), _P], _I),
+    "fermion_force": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), _D, _P], _I),
+    "gauge_action": ([_P, _D, C.POINTER(_D)], _I),
+    "gauge_force": ([_P, _D, _I, _D, _P], _I),
+    "step_T": ([_P, _P, _D], _I),
+    "step_S": ([_P, _P, _P, _D], _I),
+    "kinetic_energy": ([_P, _P, C.POINTER(_D)], _I),
+    "gaussian_draw": ([_P, _I, _I, C.c_uint64, C.c_uint64, _P], _I),
+    "metropolis": ([_D, _D, C.POINTER(_I)], _I),
+    "hmc_trajectory": ([_P, C.POINTER(wd_hmc_params), _D, C.POINTER(wd_hmc_result)], _I),
+    "wd_schedule_nested": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I, C.POINTER(_I)], _I),
+    "wd_schedule_generalised": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I,
+                                 C.POINTER(_I)], _I),
+    "wd_nmat": ([_P, C.POINTER(C.c_longlong), _I], _I),
+    "wd_profile_enable": ([_P, _I], _I),
+    "wd_profile_read": ([_P, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)], _I),
+}
+for _name, (_args, _res) in _SIG.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = sorted(_SIG)
+
+
+def _check(code):
+    if code != 0:
+        raise WdError(code, lib.wd_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def cg_params(tol=1e-10, maxiter=10000, prec=F64, delta=0.1, check_every=0):
+    return wd_cg_params(tol, maxiter, prec, delta, check_every)
+
+
+def term(kind, kappa, kappa_h=0.0, poly=None):
+    p = wd_poly(0, 0.0, 0.0) if poly is None else wd_poly(int(poly[0]), float(poly[1]), float(poly[2]))
+    return wd_term(kind, kappa, kappa_h, p)
+
+
+def _ops_array(ops):
+    arr = (wd_op * len(ops))()
+    for i, o in enumerate(ops):
+        arr[i] = wd_op(*o) if not isinstance(o, wd_op) else o
+    return arr
+
+
+def wd_schedule_nested(kind, tau, groups, steps):
+    g = (C.c_int * len(groups))(*groups)
+    s = (C.c_int * len(steps))(*steps)
+    n = C.c_int(0)
+    _check(lib.wd_schedule_nested(kind, tau, len(groups), g, s, None, 0, C.byref(n)))
+    ops = (wd_op * n.value)()
+    _check(lib.wd_schedule_nested(kind, tau, len(groups), g, s, ops, n.value, C.byref(n)))
+    return [(o.kind, o.group, o.eps) for o in ops]
+
+
+def wd_schedule_generalised(kind, tau, groups, nsteps):
+    g = (C.c_int * len(groups))(*groups)
+    s = (C.c_int * len(nsteps))(*nsteps)
+    n = C.c_int(0)
+    _check(lib.wd_schedule_generalised(kind, tau, len(groups), g, s, None, 0, C.byref(n)))
+    ops = (wd_op * n.value)()
+    _check(lib.wd_schedule_generalised(kind, tau, len(groups), g, s, ops, n.value, C.byref(n)))
+    return [(o.kind, o.group, o.eps) for o in ops]
+
+
+def metropolis(dH, u):
+    a = C.c_int(0)
+    _check(lib.metropolis(dH, u, C.byref(a)))
+    return bool(a.value)
+
+
+class Lattice:
+    """One wd_ctx: a lattice, its gauge field copies and workspaces, on the
+    current CUDA device and torch's current stream (or the given one)."""
+
+    def __init__(self, dims, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        d = (C.c_int * 4)(*self.dims)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = C.c_void_p()
+        _check(lib.wd_context_create(d, C.c_void_p(s.cuda_stream), C.byref(h)))
+        self.h = h
+        vol = (C.c_longlong * 2)()
+        _check(lib.wd_volume(self.h, vol))
+        self.V, self.Vh = int(vol[0]), int(vol[1])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.wd_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # allocation helpers (torch owns the memory)
+    def half_spinor(self, zero=True):
+        f = torch.zeros if zero else torch.empty
+        return f(24 * self.Vh, dtype=torch.float64, device=self.device)
+
+    def algebra_field(self, zero=True):
+        f = torch.zeros if zero else torch.empty
+        return f(64 * self.Vh, dtype=torch.float64, device=self.device)
+
+    # ---- entry points ----------------------------------------------------
+    def wd_set_recon(self, recon):
+        _check(lib.wd_set_recon(self.h, recon))
+
+    def wd_gauge_load(self, U_lex):
+        _check(lib.wd_gauge_load(self.h, _ptr(U_lex)))
+
+    def wd_gauge_store(self, U_lex):
+        _check(lib.wd_gauge_store(self.h, _ptr(U_lex)))
+
+    def wd_spinor_pack(self, parity, lex, eo):
+        _check(lib.wd_spinor_pack(self.h, parity, _ptr(lex), _ptr(eo)))
+
+    def wd_spinor_unpack(self, parity, eo, lex):
+        _check(lib.wd_spinor_unpack(self.h, parity, _ptr(eo), _ptr(lex)))
+
+    def wd_algebra_pack(self, lex, eo):
+        _check(lib.wd_algebra_pack(self.h, _ptr(lex), _ptr(eo)))
+
+    def wd_algebra_unpack(self, eo, lex):
+        _check(lib.wd_algebra_unpack(self.h, _ptr(eo), _ptr(lex)))
+
+    def wd_hop(self, out_parity, dagger, prec, x, out):
+        _check(lib.wd_hop(self.h, out_parity, int(dagger), prec, _ptr(x), _ptr(out)))
+
+    def wd_apply(self, kappa, dagger, prec, x, out):
+        _check(lib.wd_apply(self.h, kappa, int(dagger), prec, _ptr(x), _ptr(out)))
+
+    def mdagm_apply(self, kappa, prec, nrhs, x, out):
+        _check(lib.mdagm_apply(self.h, kappa, prec, nrhs, _ptr(x), _ptr(out)))
+
+    def cg_solve(self, kappa, b, x, params, filt=None):
+        info = wd_cg_info()
+        fp = C.byref(wd_poly(*filt)) if filt is not None else None
+        _check(lib.cg_solve(self.h, kappa, fp, _ptr(b), _ptr(x), C.byref(params), C.byref(info)))
+        return dict(iters=info.iters, reliable_updates=info.reliable_updates, n_mat=info.n_mat,
+                    true_rel_resid=info.true_rel_resid)
+
+    def poly_filter_apply(self, kappa, poly, prec, x, out):
+        _check(lib.poly_filter_apply(self.h, kappa, C.byref(wd_poly(*poly)), prec, _ptr(x), _ptr(out)))
+
+    def pf_action(self, t, phi, params):
+        S = C.c_double(0)
+        _check(lib.pf_action(self.h, C.byref(t), _ptr(phi), C.byref(params), C.byref(S)))
+        return S.value
+
+    def pf_heatbath(self, t, chi, params, phi):
+        _check(lib.pf_heatbath(self.h, C.byref(t), _ptr(chi), C.byref(params), _ptr(phi)))
+
+    def fermion_force(self, t, phi, params, coef, F):
+        _check(lib.fermion_force(self.h, C.byref(t), _ptr(phi), C.byref(params), coef, _ptr(F)))
+
+    def gauge_action(self, beta):
+        S = C.c_double(0)
+        _check(lib.gauge_action(self.h, beta, C.byref(S)))
+        return S.value
+
+    def gauge_force(self, beta, prec, coef, F):
+        _check(lib.gauge_force(self.h, beta, prec, coef, _ptr(F)))
+
+    def step_T(self, P, eps):
+        _check(lib.step_T(self.h, _ptr(P), eps))
+
+    def step_S(self, P, F, eps):
+        _check(lib.step_S(self.h, _ptr(P), _ptr(F), eps))
+
+    def kinetic_energy(self, P):
+        K = C.c_double(0)
+        _check(lib.kinetic_energy(self.h, _ptr(P), C.byref(K)))
+        return K.value
+
+    def gaussian_draw(self, what, parity, seed, stream, out):
+        _check(lib.gaussian_draw(self.h, what, parity, seed, stream, _ptr(out)))
+
+    def hmc_trajectory(self, terms, groups, beta, ops, cg_md, cg_acc, force_prec, seed, traj_index, u):
+        tarr = (wd_term * max(len(terms), 1))(*terms)
+        garr = (C.c_int * max(len(groups), 1))(*groups)
+        oarr = _ops_array(ops)
+        p = wd_hmc_params(len(terms), tarr, garr, beta, len(ops), oarr, cg_md, cg_acc, force_prec, seed,
+                          traj_index)
+        r = wd_hmc_result()
+        _check(lib.hmc_trajectory(self.h, C.byref(p), u, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in wd_hmc_result._fields_}
+
+    def wd_nmat(self, reset=False):
+        n = C.c_longlong(0)
+        _check(lib.wd_nmat(self.h, C.byref(n), int(reset)))
+        return n.value
+
+    def wd_profile_enable(self, every_n):
+        _check(lib.wd_profile_enable(self.h, every_n))
+
+    def wd_profile_read(self):
+        n, ms, b = C.c_longlong(0), C.c_double(0), C.c_double(0)
+        _check(lib.wd_profile_read(self.h, C.byref(n), C.byref(ms), C.byref(b)))
+        return dict(launches=n.value, ms=ms.value, bytes=b.value)

@@ -1,0 +1,191 @@
+"""GPU parity of actions, heat bath, fermion and gauge forces, HMC steps,
+Gaussian draws and a whole trajectory, against the oracle.
+
+Tolerances: actions and heat bath 1e-10 relative; FP64 forces 1e-9
+(Frobenius, relative); FP32 forces 1e-5; gauge action 1e-12; T step 1e-13
+per link; Gaussian draws 1e-13 (same Philox words, transcendental rounding
+differs); trajectory dH 1e-9 absolute and final links 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import actions, force, hmc, lattice, philox, wilson
+from oracle.poly import ChebyshevFilter
+from paper_1702_00124_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+POLY = (4, 0.05, 5.0)
+KAPPA, KAPPA_H = 0.125, 0.115
+
+
+def _oracle_term(kind):
+    pf = ChebyshevFilter(*POLY)
+    return {0: actions.term("plain", KAPPA), 1: actions.term("hasenbusch", KAPPA, KAPPA_H),
+            2: actions.term("poly", KAPPA_H, poly=pf), 3: actions.term("filtered", KAPPA_H, poly=pf)}[kind]
+
+
+def _gpu_term(wd, kind):
+    return {0: wd.term(wd.PLAIN, KAPPA), 1: wd.term(wd.HASENBUSCH, KAPPA, KAPPA_H),
+            2: wd.term(wd.POLY, KAPPA_H, poly=POLY), 3: wd.term(wd.FILTERED, KAPPA_H, poly=POLY)}[kind]
+
+
+@pytest.fixture(scope="module", params=[(4, 4, 4, 4), (6, 4, 6, 10)], ids=["4x4x4x4", "6x4x6x10"])
+def setup(request):
+    from paper_1702_00124_gb300 import wdhmc
+    from tests import gpu_util as gu
+    dims = request.param
+    U = synthetic.gauge_field(dims, 0.5, 501 + dims[3])
+    chi = lattice.mask(synthetic.spinor_field(dims, 502 + dims[3]), dims, 0)
+    lat = wdhmc.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U))
+    yield dict(dims=dims, U=U, chi=chi, lat=lat, gu=gu, wd=wdhmc)
+    lat.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["plain", "hasenbusch", "poly", "filtered"])
+def test_heatbath_and_action(setup, kind):
+    s = setup
+    lat, gu, wd = s["lat"], s["gu"], s["wd"]
+    t_o, t_g = _oracle_term(kind), _gpu_term(wd, kind)
+    phi_ref = actions.heatbath(s["U"], t_o, s["chi"])
+    chi_e = gu.pack(lat, s["chi"], 0)
+    phi = lat.half_spinor()
+    lat.pf_heatbath(t_g, chi_e, wd.cg_params(tol=1e-13), phi)
+    assert gu.rel_norm_err(gu.unpack(lat, phi, 0), phi_ref) < 1e-10
+    S_ref, _ = actions.action(s["U"], t_o, phi_ref)
+    for prec in (0, 1):
+        S = lat.pf_action(t_g, phi, wd.cg_params(tol=1e-11, prec=prec))
+        assert abs(S - S_ref) < 1e-10 * abs(S_ref), (prec, S, S_ref)
+    chi2 = float(np.vdot(s["chi"], s["chi"]).real)
+    assert abs(S_ref - chi2) < 1e-9 * chi2
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["plain", "hasenbusch", "poly", "filtered"])
+def test_fermion_force(setup, kind):
+    s = setup
+    lat, gu, wd = s["lat"], s["gu"], s["wd"]
+    t_o, t_g = _oracle_term(kind), _gpu_term(wd, kind)
+    phi = s["chi"]                      # any even field serves as phi
+    F_ref = force.fermion_force(s["U"], t_o, phi)
+    phi_e = gu.pack(lat, phi, 0)
+    for prec, tol in ((0, 1e-9), (1, 1e-5)):
+        F = lat.algebra_field()
+        lat.fermion_force(t_g, phi_e, wd.cg_params(tol=1e-13 if prec == 0 else 1e-10, prec=prec), 1.0, F)
+        Fg = gu.alg_to_host(lat, F)
+        err = np.linalg.norm(Fg - F_ref) / np.linalg.norm(F_ref)
+        assert err < tol, (prec, err)
+    # coef scales and accumulates: F += 2 * force on top of -1 * force gives +1 * force
+    F = lat.algebra_field()
+    p = wd.cg_params(tol=1e-13)
+    lat.fermion_force(t_g, phi_e, p, -1.0, F)
+    lat.fermion_force(t_g, phi_e, p, 2.0, F)
+    assert np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) < 1e-9 * np.linalg.norm(F_ref)
+
+
+def test_gauge_action_and_force(setup):
+    s = setup
+    lat, gu = s["lat"], s["gu"]
+    beta = 5.6
+    S_ref = force.gauge_action(s["U"], beta)
+    assert abs(lat.gauge_action(beta) - S_ref) < 1e-12 * S_ref
+    F_ref = force.gauge_force(s["U"], beta)
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        F = lat.algebra_field()
+        lat.gauge_force(beta, prec, 1.0, F)
+        err = np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) / np.linalg.norm(F_ref)
+        assert err < tol, (prec, err)
+
+
+def test_steps_and_kinetic(setup):
+    s = setup
+    lat, gu = s["lat"], s["gu"]
+    P = synthetic.momenta(s["dims"], 77)
+    Pe = gu.alg_to_dev(lat, P)
+    assert abs(lat.kinetic_energy(Pe) - hmc.kinetic(P)) < 1e-12 * hmc.kinetic(P)
+    import torch
+    for eps in (0.3, 0.01, 1e-4):
+        lat.wd_gauge_load(gu.dev(s["U"]))
+        lat.step_T(Pe, eps)
+        Ub = torch.zeros(2 * s["U"].size, dtype=torch.float64, device="cuda")
+        lat.wd_gauge_store(Ub)
+        ref = hmc.step_T(s["U"], P, eps)
+        assert np.max(np.abs(gu.host_c(Ub, s["U"].shape) - ref)) < 1e-13
+    lat.wd_gauge_load(gu.dev(s["U"]))
+    F = gu.alg_to_dev(lat, synthetic.momenta(s["dims"], 78))
+    lat.step_S(Pe, F, 0.25)
+    assert np.max(np.abs(gu.alg_to_host(lat, Pe) - hmc.step_S(P, synthetic.momenta(s["dims"], 78), 0.25))) < 1e-14
+
+
+def test_gaussian_draws(setup):
+    s = setup
+    lat, gu = s["lat"], s["gu"]
+    dims = s["dims"]
+    V = int(np.prod(dims))
+    seed, stream = 424242, 9
+    out = lat.algebra_field()
+    lat.gaussian_draw(1, 0, seed, stream, out)
+    ref = philox.gaussian_field(V * 32, seed, stream).reshape(lattice.shape(dims) + (4, 8))
+    assert np.max(np.abs(gu.alg_to_host(lat, out) - ref)) < 1e-13
+    for par in (0, 1):
+        h = lat.half_spinor()
+        lat.gaussian_draw(0, par, seed, stream + 1, h)
+        g = philox.gaussian_field(V * 24, seed, stream + 1)
+        ref = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, par)
+        assert np.max(np.abs(gu.unpack(lat, h, par) - ref)) < 1e-13
+
+
+def test_trajectory_matches_oracle():
+    """One PF-MP + gauge trajectory with a nested Omelyan 2MN schedule, every
+    step in FP64: same draws (Philox), same schedule structure (the GPU merges
+    commuting S steps, the oracle does not), dH and final links compared."""
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 4)
+    U0 = synthetic.gauge_field(dims, 0.3, 901)
+    k, kh, beta, tau = 0.124, 0.115, 5.6, 0.4
+    seed, traj = 123, 5
+    pf = ChebyshevFilter(*POLY)
+    terms_o = [actions.term("poly", kh, poly=pf), actions.term("filtered", kh, poly=pf),
+               actions.term("hasenbusch", k, kh)]
+    terms_g = [wd.term(wd.POLY, kh, poly=POLY), wd.term(wd.FILTERED, kh, poly=POLY),
+               wd.term(wd.HASENBUSCH, k, kh)]
+    groups = [1, 0, 0]                     # group 0 outer: filtered + hasenbusch; 1: poly; -1: gauge
+    levels = [(0, 2), (1, 2), (-1, 2)]
+    ops_g = wd.wd_schedule_nested(1, tau, [g for g, _ in levels], [n for _, n in levels])
+    ops_o = hmc.nested(levels, tau, "omelyan")
+    V = int(np.prod(dims))
+    base = traj * 64
+    P0 = philox.gaussian_field(V * 32, seed, base).reshape(lattice.shape(dims) + (4, 8))
+    phis = []
+    for i, t in enumerate(terms_o):
+        g = philox.gaussian_field(V * 24, seed, base + 1 + i)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        phis.append(actions.heatbath(U0, t, chi))
+
+    def H(U, P):
+        return hmc.kinetic(P) + force.gauge_action(U, beta) + sum(
+            actions.action(U, t, ph)[0] for t, ph in zip(terms_o, phis))
+
+    def fog(grp, U):
+        if grp == -1:
+            return force.gauge_force(U, beta)
+        return sum(force.fermion_force(U, t, ph) for t, ph, g in zip(terms_o, phis, groups) if g == grp)
+
+    U1, P1 = hmc.integrate(U0, P0, ops_o, fog)
+    dH_ref = H(U1, P1) - H(U0, P0)
+
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U0))
+    p64 = wd.cg_params(tol=1e-14, maxiter=20000)
+    r = lat.hmc_trajectory(terms_g, groups, beta, ops_g, p64, p64, wd.F64, seed, traj, 0.0)
+    assert abs(r["dH"] - dH_ref) < 1e-9, (r["dH"], dH_ref)
+    import torch
+    Ub = torch.zeros(2 * U0.size, dtype=torch.float64, device="cuda")
+    lat.wd_gauge_store(Ub)
+    if r["accepted"]:
+        assert np.max(np.abs(gu.host_c(Ub, U0.shape) - U1)) < 1e-10
+    else:
+        assert np.array_equal(gu.host_c(Ub, U0.shape), U0)
+    assert r["n_mat"] > 0
+    lat.close()
