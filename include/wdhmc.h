@@ -16,8 +16,11 @@
  * Conventions for every call
  *   - Every pointer to field data is DEVICE memory owned by the caller unless
  *     the comment says "host".  The library never frees caller memory.
- *   - The library allocates device memory only in wd_context_create (its
- *     workspaces and the gauge field copies).
+ *   - The library allocates device memory in wd_context_create (gauge field
+ *     copies, reduction scratch) and, the first time an operation needs more
+ *     half-lattice workspace vectors than the context holds, grows the
+ *     context's pool (cudaMalloc); the pool is kept until
+ *     wd_context_destroy, so repeated calls allocate nothing.
  *   - Work is ordered on the stream given to wd_context_create.  Calls that
  *     return a scalar to a host pointer synchronise that stream.
  *   - Return value: WD_OK or an error code; wd_last_error() gives a message.
@@ -237,10 +240,16 @@ int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups
 /* N_mat: K_hat applications since the context was created or reset. */
 int wd_nmat(wd_ctx* ctx, long long* count, int reset);
 /* Sample every n-th launch of the hop kernels with CUDA events on the context
- * stream (n = 0 disables).  wd_profile_read gives the sampled launches, their
- * total device time (ms) and the algorithmic bytes of those launches. */
+ * stream (n = 0 disables; launches queued inside a CG chunk, which may return
+ * early after convergence, are not sampled).  wd_profile_read gives, for the
+ * hop kernels whose input spinors have format fmt (enum wd_prec, or -1 for
+ * all), the sampled launches, their total device time (ms) and the
+ * algorithmic bytes of those launches (every input site, link and output site
+ * moved once). */
 int wd_profile_enable(wd_ctx* ctx, int every_n);
-int wd_profile_read(wd_ctx* ctx, long long* launches, double* total_ms, double* bytes);
+int wd_profile_read(wd_ctx* ctx, int fmt, long long* launches, double* total_ms, double* bytes);
+/* Kernels launched by this context since it was created. */
+int wd_launch_count(wd_ctx* ctx, long long* count);
 
 #ifdef __cplusplus
 }

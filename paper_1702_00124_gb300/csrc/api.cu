@@ -273,35 +273,53 @@ int wd_nmat(wd_ctx* c, long long* count, int reset) {
 int wd_profile_enable(wd_ctx* c, int every_n) {
   CHECK_CTX(c);
   if (every_n < 0) return fail(WD_ERR_ARG, "every_n must be >= 0");
-  c->prof.every = every_n;
-  c->prof.seen = 0;
-  c->prof.launches = 0;
-  c->prof.ms = 0.0;
-  c->prof.bytes = 0.0;
-  for (auto& e : c->prof.ev) cudaEventDestroy(e);
-  c->prof.ev.clear();
-  c->prof.ev_bytes.clear();
+  Prof& p = c->prof;
+  p.every = every_n;
+  p.seen = 0;
+  for (int f = 0; f < 4; ++f) { p.launches[f] = 0; p.ms[f] = 0.0; p.bytes[f] = 0.0; }
+  for (auto& e : p.ev) cudaEventDestroy(e);
+  p.ev.clear();
+  p.ev_bytes.clear();
+  p.ev_fmt.clear();
   return WD_OK;
 }
 
-int wd_profile_read(wd_ctx* c, long long* launches, double* total_ms, double* bytes) {
+int wd_profile_read(wd_ctx* c, int fmt, long long* launches, double* total_ms, double* bytes) {
   CHECK_CTX(c);
+  if (fmt < -1 || fmt > WD_BF16) return fail(WD_ERR_ARG, "fmt must be -1 (all) or a wd_prec");
   Prof& p = c->prof;
   for (size_t k = 0; k + 1 < p.ev.size(); k += 2) {
     float ms = 0.f;
     WD_CUDA(cudaEventSynchronize(p.ev[k + 1]));
     WD_CUDA(cudaEventElapsedTime(&ms, p.ev[k], p.ev[k + 1]));
-    p.ms += ms;
-    p.bytes += p.ev_bytes[k / 2];
-    p.launches += 1;
+    const int f = p.ev_fmt[k / 2];
+    p.ms[f] += ms;
+    p.bytes[f] += p.ev_bytes[k / 2];
+    p.launches[f] += 1;
     cudaEventDestroy(p.ev[k]);
     cudaEventDestroy(p.ev[k + 1]);
   }
   p.ev.clear();
   p.ev_bytes.clear();
-  if (launches) *launches = p.launches;
-  if (total_ms) *total_ms = p.ms;
-  if (bytes) *bytes = p.bytes;
+  p.ev_fmt.clear();
+  long long n = 0;
+  double ms = 0, b = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (fmt >= 0 && f != fmt) continue;
+    n += p.launches[f];
+    ms += p.ms[f];
+    b += p.bytes[f];
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  if (bytes) *bytes = b;
+  return WD_OK;
+}
+
+int wd_launch_count(wd_ctx* c, long long* count) {
+  CHECK_CTX(c);
+  CHECK_PTR(count);
+  *count = c->launches;
   return WD_OK;
 }
 

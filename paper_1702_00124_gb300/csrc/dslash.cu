@@ -39,7 +39,7 @@ void prof_begin(wd_ctx* c, cudaEvent_t* e0) {
   *e0 = e;
 }
 
-void prof_end(wd_ctx* c, cudaEvent_t e0, double bytes) {
+void prof_end(wd_ctx* c, cudaEvent_t e0, double bytes, int fmt) {
   if (e0 == nullptr) return;
   cudaEvent_t e1;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
@@ -47,19 +47,22 @@ void prof_end(wd_ctx* c, cudaEvent_t e0, double bytes) {
   c->prof.ev.push_back(e0);
   c->prof.ev.push_back(e1);
   c->prof.ev_bytes.push_back(bytes);
+  c->prof.ev_fmt.push_back(fmt);
 }
 
 int hop(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
         double alpha, bool norm_cg, bool in_cg) {
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
-  cudaEvent_t e0;
-  prof_begin(c, &e0);
+  // Launches queued inside a CG chunk may return at once after convergence;
+  // only launches that always do their work are sampled.
+  cudaEvent_t e0 = nullptr;
+  if (!in_cg) prof_begin(c, &e0);
   int s;
   if (in.fmt == WD_F64) s = hop_f64(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   else if (in.fmt == WD_F32) s = hop_f32(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   else s = hop_h16(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   if (s != WD_OK) return s;
-  prof_end(c, e0, hop_bytes(in.fmt, out.fmt, y != nullptr, gauge_link_bytes(c, in.fmt), c->g.Vh));
+  prof_end(c, e0, hop_bytes(in.fmt, out.fmt, y != nullptr, gauge_link_bytes(c, in.fmt), c->g.Vh), in.fmt);
   return WD_OK;
 }
 

@@ -145,14 +145,25 @@ static int true_residual(wd_ctx* c, const Op& op, const Field& b, const Field& x
   return norm2(c, r, rr);
 }
 
+// Default reliable-update factor per sloppy precision: the iterated residual
+// of FP32 stays faithful over larger reductions than that of 16-bit storage.
+static double default_delta(int prec) {
+  switch (prec) {
+    case WD_F32: return 1e-2;
+    case WD_F16: return 5e-2;
+    case WD_BF16: return 1e-1;
+    default: return 1e-1;
+  }
+}
+
 static int cg_core(wd_ctx* c, const Op& op, const Field& b, const Field& x, const wd_cg_params& p,
-                   wd_cg_info* info) {
+                   wd_cg_info* info, bool x_zero = false) {
   if (!(p.tol > 0) || p.maxiter < 1) return fail(WD_ERR_ARG, "cg: tol must be > 0 and maxiter >= 1");
   int prec = p.prec;
   if (prec < WD_F64 || prec > WD_BF16) return fail(WD_ERR_ARG, "cg: unknown precision");
   if (op.kind != OP_K && (prec == WD_F16 || prec == WD_BF16)) prec = WD_F32;  // poly in FP32
   const int accf = (prec == WD_F64) ? WD_F64 : WD_F32;
-  const double delta = (p.delta > 0 && p.delta < 1) ? p.delta : 0.1;
+  const double delta = (p.delta > 0 && p.delta < 1) ? p.delta : default_delta(prec);
   const int check = p.check_every > 0 ? p.check_every : (op.kind == OP_K ? 16 : 1);
   const long long nmat0 = c->nmat;
 
@@ -170,7 +181,13 @@ static int cg_core(wd_ctx* c, const Op& op, const Field& b, const Field& x, cons
   WD_TRY(w.get(WD_F64, &r));
   WD_TRY(w.get(WD_F64, &t));
   double rr;
-  WD_TRY(true_residual(c, op, b, x, r, t, &rr));
+  if (x_zero) {   // r = b without applying A
+    WD_TRY(zero(c, x));
+    WD_TRY(convert(c, b, r));
+    rr = bb;
+  } else {
+    WD_TRY(true_residual(c, op, b, x, r, t, &rr));
+  }
   if (!std::isfinite(rr)) return fail(WD_ERR_NAN, "cg: non-finite initial residual");
   int status = WD_OK;
   if (rr > stop_rr) {
@@ -226,22 +243,22 @@ static int cg_core(wd_ctx* c, const Op& op, const Field& b, const Field& x, cons
 }
 
 int cg_solve_f(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, const Field& x,
-               const wd_cg_params& p, wd_cg_info* info) {
+               const wd_cg_params& p, wd_cg_info* info, bool x_zero) {
   Op op{filt ? OP_KP : OP_K, kappa, filt ? *filt : wd_poly{0, 0, 0}};
   if (filt) {
     PolyCoef pc;
     WD_TRY(poly_coef(*filt, &pc));
   }
-  return cg_core(c, op, b, x, p, info);
+  return cg_core(c, op, b, x, p, info, x_zero);
 }
 
-// CG on P(K_hat) (heat bath of the polynomial term)
+// CG on P(K_hat) (heat bath of the polynomial term), from x = 0
 int cg_solve_poly(wd_ctx* c, double kappa, const wd_poly& P, const Field& b, const Field& x,
                   const wd_cg_params& p, wd_cg_info* info) {
   PolyCoef pc;
   WD_TRY(poly_coef(P, &pc));
   Op op{OP_P, kappa, P};
-  return cg_core(c, op, b, x, p, info);
+  return cg_core(c, op, b, x, p, info, true);
 }
 
 }  // namespace wd

@@ -131,9 +131,8 @@ static int apply_cdag(wd_ctx* c, double kappa, const PolyCoef& pc, const Field& 
 
 static int solve(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, const Field& x,
                  const wd_cg_params& p) {
-  WD_TRY(zero(c, x));
   wd_cg_info info;
-  return cg_solve_f(c, kappa, filt, b, x, p, &info);
+  return cg_solve_f(c, kappa, filt, b, x, p, &info, true);
 }
 
 int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double* S) {

@@ -313,14 +313,16 @@ struct Field {
 
 size_t field_bytes(int fmt, long Vh);
 
+// Sampled launch timing of the hop kernels, per input-spinor format.
 struct Prof {
   int every = 0;
   long long seen = 0;
-  long long launches = 0;
-  double ms = 0.0;
-  double bytes = 0.0;
+  long long launches[4] = {0, 0, 0, 0};
+  double ms[4] = {0, 0, 0, 0};
+  double bytes[4] = {0, 0, 0, 0};
   std::vector<cudaEvent_t> ev;   // pairs, pending
   std::vector<double> ev_bytes;
+  std::vector<int> ev_fmt;
 };
 
 }  // namespace wd
@@ -349,6 +351,7 @@ struct wd_ctx {
   std::vector<wd::Field> pool;
   std::vector<bool> pool_used;
   long long nmat = 0;
+  long long launches = 0;           // kernels launched by the library
   wd::Prof prof;
 };
 
@@ -363,7 +366,12 @@ int cuda_fail(cudaError_t e, const char* what);
     cudaError_t _e = (call);                                  \
     if (_e != cudaSuccess) return ::wd::cuda_fail(_e, #call); \
   } while (0)
-#define WD_CHECK_LAUNCH() WD_CUDA(cudaGetLastError())
+// after every kernel launch: count it (context `c` in scope) and check it
+#define WD_CHECK_LAUNCH()                   \
+  do {                                      \
+    c->launches += 1;                       \
+    WD_CUDA(cudaGetLastError());            \
+  } while (0)
 #define WD_TRY(expr)                      \
   do {                                    \
     int _s = (expr);                      \
@@ -419,8 +427,9 @@ int gamma5(wd_ctx* c, const Field& in, const Field& out);
 int khat_any(wd_ctx* c, double kappa, const Field& in, const Field& out);   // FP64 fields
 int poly_apply_f(wd_ctx* c, double kappa, const wd_poly& P, int prec, const Field& in,
                  const Field& out);
+// x_zero: start from x = 0 (x is zeroed, the initial residual is b itself)
 int cg_solve_f(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, const Field& x,
-               const wd_cg_params& p, wd_cg_info* info);
+               const wd_cg_params& p, wd_cg_info* info, bool x_zero = false);
 int cg_solve_poly(wd_ctx* c, double kappa, const wd_poly& P, const Field& b, const Field& x,
                   const wd_cg_params& p, wd_cg_info* info);
 
@@ -452,6 +461,6 @@ int poly_coef(const wd_poly& P, PolyCoef* out);
 // launch helpers
 inline int nblocks(long n, int threads) { return (int)((n + threads - 1) / threads); }
 void prof_begin(wd_ctx* c, cudaEvent_t* e0);
-void prof_end(wd_ctx* c, cudaEvent_t e0, double bytes);
+void prof_end(wd_ctx* c, cudaEvent_t e0, double bytes, int fmt);
 
 }  // namespace wd

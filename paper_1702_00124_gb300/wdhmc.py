@@ -100,7 +100,8 @@ _SIG = {
                                  C.POINTER(_I)], _I),
     "wd_nmat": ([_P, C.POINTER(C.c_longlong), _I], _I),
     "wd_profile_enable": ([_P, _I], _I),
-    "wd_profile_read": ([_P, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)], _I),
+    "wd_profile_read": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)], _I),
+    "wd_launch_count": ([_P, C.POINTER(C.c_longlong)], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -127,7 +128,8 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def cg_params(tol=1e-10, maxiter=10000, prec=F64, delta=0.1, check_every=0):
+def cg_params(tol=1e-10, maxiter=10000, prec=F64, delta=0.0, check_every=0):
+    """delta = 0 and check_every = 0 select the library defaults."""
     return wd_cg_params(tol, maxiter, prec, delta, check_every)
 
 
@@ -298,7 +300,12 @@ class Lattice:
     def wd_profile_enable(self, every_n):
         _check(lib.wd_profile_enable(self.h, every_n))
 
-    def wd_profile_read(self):
+    def wd_profile_read(self, fmt=-1):
         n, ms, b = C.c_longlong(0), C.c_double(0), C.c_double(0)
-        _check(lib.wd_profile_read(self.h, C.byref(n), C.byref(ms), C.byref(b)))
+        _check(lib.wd_profile_read(self.h, fmt, C.byref(n), C.byref(ms), C.byref(b)))
         return dict(launches=n.value, ms=ms.value, bytes=b.value)
+
+    def wd_launch_count(self):
+        n = C.c_longlong(0)
+        _check(lib.wd_launch_count(self.h, C.byref(n)))
+        return n.value
