@@ -48,7 +48,7 @@ LEVELS = [(0, 10), (1, 1), (-1, 2)]
 # K_hat applications of one trajectory of the default workload, counted by
 # the library's N_mat counter (algorithmic count; the reference arm scales
 # its per-K_hat time by it).
-N_MAT_PER_TRAJ = 33000
+N_MAT_PER_TRAJ = 19350
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hop_f32_c5_32x32x32x64.md")
 
 
@@ -164,6 +164,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def kernel_case(args):
+    """K_hat alone on the workload's lattice: the launch sequence ncu captures."""
+    import torch
+    from paper_1702_00124_gb300 import synthetic, wdhmc as wd
+    w = WORKLOADS[args.workload]
+    dims = w["dims"]
+    U = synthetic.gauge_field(dims, w["a"], synthetic.SEED_BASE + 4)
+    lat = wd.Lattice(dims)
+    U_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda")
+    lat.wd_gauge_load(U_dev)
+    del U_dev
+    prec, recon = {"khat_f32_recon12": (wd.F32, 1), "khat_bf16_recon12": (wd.BF16, 1),
+                   "khat_f64": (wd.F64, 0)}[args.kernel_case]
+    lat.wd_set_recon(recon)
+    x, y = lat.half_spinor(), lat.half_spinor()
+    lat.gaussian_draw(0, 0, 1, 1, x)
+    for _ in range(args.reps):
+        lat.mdagm_apply(w["kappa"], prec, 1, x, y)
+    torch.cuda.synchronize()
+    lat.close()
+    print(f"kernel case {args.kernel_case} on {args.workload}: {args.reps} K_hat applications")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,12 +195,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-vs-FP64 and e2e measurements")
+    ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64"],
+                    help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
+    ap.add_argument("--reps", type=int, default=4)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.kernel_case:
+        return kernel_case(args)
 
     import torch
     from paper_1702_00124_gb300 import synthetic, wdhmc as wd
