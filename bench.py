@@ -249,7 +249,9 @@ def main():
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    lat.wd_profile_enable(8)
+    # every 7th hop launch: co-prime with the 4-hop cycle of K_hat, so every
+    # variant (plain, xpay, dagger) is sampled
+    lat.wd_profile_enable(7)
     l0, n0 = lat.wd_launch_count(), lat.wd_nmat()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
