@@ -235,6 +235,31 @@ int wd_schedule_nested(int kind, double tau, int nlevels, const int* groups, con
 int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups,
                             const int* nsteps, wd_op* ops, int cap, int* nops);
 
+/* ---- allocation-free K_hat ----------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: code whose device memory belongs to a host
+ * application's own pool manager, latency-critical code that cannot afford the
+ * implicit device-wide synchronisation of cudaMalloc, or code that must not fail
+ * on allocation under memory pressure.  It needs no context.
+ *
+ * out = K_hat in = M_hat^dag M_hat in (FP64, even sites), M_hat = 1 - kappa^2 D_eo D_oe.
+ *   dims      {Lx, Ly, Lz, Lt}, even, >= 2, with V/2 <= 32768 sites per parity
+ *             (e.g. 16^4); larger lattices return WD_ERR_ARG before any launch.
+ *   gauge_eo  device, FP64 links in the even-odd layout
+ *             complex double [4 mu][2 parity][9 = 3 row + col][Vh] (the layout of
+ *             the context's own FP64 copy): U_mu(x) of the site with parity p and
+ *             checkerboard index cb at element ((mu*2 + p)*9 + 3*row + col)*Vh + cb.
+ *   in, out   device half spinors (double2 [12][Vh]); may be the same buffer.
+ *   stream    cudaStream_t or NULL; the call is asynchronous on it.
+ * Allocates nothing: the two intermediate half spinors live in one static device
+ * array (12.6 MB) held on every device that loads the library until exit.
+ * Every call shares that array and overwrites it; calls that overlap on the
+ * GPU race on it and must be serialised by the caller.  The first call on a
+ * device looks up the array's address with that device current; make that
+ * first call before any stream capture. */
+int mdagm_apply_noalloc(const int dims[4], const double* gauge_eo, double kappa, const double* in,
+                        double* out, void* stream);
+
 /* ---- counters and timing ---------------------------------------------------- */
 
 /* N_mat: K_hat applications since the context was created or reset. */

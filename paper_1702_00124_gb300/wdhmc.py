@@ -102,6 +102,7 @@ _SIG = {
     "wd_profile_enable": ([_P, _I], _I),
     "wd_profile_read": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)], _I),
     "wd_launch_count": ([_P, C.POINTER(C.c_longlong)], _I),
+    "mdagm_apply_noalloc": ([C.POINTER(C.c_int), _P, _D, _P, _P, _P], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
