@@ -169,6 +169,19 @@ int pf_heatbath(wd_ctx* ctx, const wd_term* term, const double* chi, const wd_cg
  * per term; polynomial intermediates are recomputed from checkpoints. */
 int fermion_force(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
                   double coef, double* F);
+/* pf_action that also returns the vectors the force needs (differentiation
+ * without re-solving): X = A^-1 psi (psi = phi, or M_h^dag phi for
+ * HASENBUSCH; A = K_hat, or K_hat P(K_hat) for FILTERED) and, for PLAIN and
+ * HASENBUSCH, Y = M_hat X.  X and Y are caller half spinors or NULL (not
+ * written for POLY / not needed). */
+int pf_action_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
+                 double* S, double* X, double* Y);
+/* F += coef * dS/dw from the X (and Y) of pf_action_xy: the adjoint of the
+ * action without a solve (Section 2, fermion force; only X and Y are kept per
+ * term, polynomial-term vectors are recomputed).  Y may be NULL (formed from
+ * X); POLY needs neither.  prec: WD_F64 or WD_F32 arithmetic. */
+int fermion_force_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const double* X,
+                     const double* Y, int prec, double coef, double* F);
 /* Wilson plaquette action S_G = beta sum (1 - Re tr U_p / 3); *S host. */
 int gauge_action(wd_ctx* ctx, double beta, double* S);
 /* F += coef * dS_G/dw. */

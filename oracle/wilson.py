@@ -30,12 +30,18 @@ from .lattice import shift, mask, dims_of
 
 
 def _colour(Umat, psi):
-    """U psi on every spin component: U[...,a,b] psi[...,s,b]."""
-    return np.einsum("...ab,...sb->...sa", Umat, psi)
+    """U psi on every spin component: (U psi_s)_a = sum_b U[...,a,b] psi[...,s,b]."""
+    return np.matmul(psi, np.swapaxes(Umat, -1, -2))
 
 
 def _colour_dag(Umat, psi):
-    return np.einsum("...ba,...sb->...sa", Umat.conj(), psi)
+    """U^dag psi on every spin component: sum_b conj(U[...,b,a]) psi[...,s,b]."""
+    return np.matmul(psi, Umat.conj())
+
+
+def _spin(g, psi):
+    """(g psi)_s = sum_t g[s,t] psi[...,t,c]."""
+    return np.matmul(g, psi)
 
 
 def hop(U, psi, dagger=False):
@@ -45,10 +51,10 @@ def hop(U, psi, dagger=False):
     for mu in range(4):
         g = GAMMA[mu].astype(psi.dtype)
         fw = _colour(U[..., mu, :, :], shift(psi, mu, +1, antiperiodic=True))
-        out += fw + sgn * np.einsum("st,...tc->...sc", g, fw)
+        out += fw + sgn * _spin(g, fw)
         Ub = shift(U[..., mu, :, :], mu, -1)
         bw = _colour_dag(Ub, shift(psi, mu, -1, antiperiodic=True))
-        out += bw - sgn * np.einsum("st,...tc->...sc", g, bw)
+        out += bw - sgn * _spin(g, bw)
     return out
 
 

@@ -135,7 +135,10 @@ static int solve(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, c
   return cg_solve_f(c, kappa, filt, b, x, p, &info, true);
 }
 
-int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double* S) {
+// S of one term; when Xo / Yo are given, also the solution X = A^-1 psi and
+// (PLAIN, HASENBUSCH) Y = M_hat X, the only vectors the force needs.
+int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double* S,
+                const Field* Xo = nullptr, const Field* Yo = nullptr) {
   WsGuard w(c);
   Field b, X, AX, tmp;
   WD_TRY(w.get(WD_F64, &b));
@@ -152,6 +155,8 @@ int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_param
       WD_TRY(dot(c, b, X, &re, nullptr));
       WD_TRY(norm2(c, AX, &xax));
       *S = 2.0 * re - xax;
+      if (Xo) WD_TRY(convert(c, X, *Xo));
+      if (Yo) WD_TRY(convert(c, AX, *Yo));
       return WD_OK;
     }
     case WD_TERM_POLY: {
@@ -168,6 +173,7 @@ int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_param
       WD_TRY(dot(c, phi, X, &re, nullptr));
       WD_TRY(dot(c, X, AX, &xax, nullptr));
       *S = 2.0 * re - xax;
+      if (Xo) WD_TRY(convert(c, X, *Xo));
       return WD_OK;
     }
   }
@@ -204,22 +210,20 @@ int term_heatbath(wd_ctx* c, const wd_term& t, const Field& chi, const wd_cg_par
   return fail(WD_ERR_ARG, "unknown term kind");
 }
 
-int term_force(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double coef, double* F) {
-  const int f = force_fmt(p);
+// Force from a given solution X (and Y = M_hat X, or nullptr to form it):
+// no solve.  POLY ignores X and Y.  f = FP64 or FP32 arithmetic.
+int term_force_xy(wd_ctx* c, const wd_term& t, const Field& phi, const Field* X, const Field* Y, int f,
+                  double coef, double* F) {
   WsGuard w(c);
-  Field b, X, Xf, Yf, phif;
-  WD_TRY(w.get(WD_F64, &X));
+  Field Xf, Yf, phif;
   switch (t.kind) {
     case WD_TERM_PLAIN:
     case WD_TERM_HASENBUSCH: {
-      WD_TRY(w.get(WD_F64, &b));
-      if (t.kind == WD_TERM_PLAIN) WD_TRY(convert(c, phi, b));
-      else WD_TRY(mhat(c, t.kappa_h, true, phi, b));
-      WD_TRY(solve(c, t.kappa, nullptr, b, X, p));
       WD_TRY(w.get(f, &Xf));
       WD_TRY(w.get(f, &Yf));
-      WD_TRY(convert(c, X, Xf));
-      WD_TRY(mhat(c, t.kappa, false, Xf, Yf));
+      WD_TRY(convert(c, *X, Xf));
+      if (Y) WD_TRY(convert(c, *Y, Yf));
+      else WD_TRY(mhat(c, t.kappa, false, Xf, Yf));
       WD_TRY(mhat_outer(c, t.kappa, Yf, Xf, -2.0 * coef, F));
       if (t.kind == WD_TERM_HASENBUSCH) {
         WD_TRY(w.get(f, &phif));
@@ -238,14 +242,35 @@ int term_force(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params
     case WD_TERM_FILTERED: {
       PolyCoef pc;
       WD_TRY(poly_coef(t.poly, &pc));
-      WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
       WD_TRY(w.get(f, &Xf));
-      WD_TRY(convert(c, X, Xf));
+      WD_TRY(convert(c, *X, Xf));
       std::vector<double> rr(1, 0.0), ri(1, 0.0);
       rr.insert(rr.end(), pc.zr.begin(), pc.zr.end());
       ri.insert(ri.end(), pc.zi.begin(), pc.zi.end());
       return poly_force(c, t.kappa, rr, ri, pc.scale, Xf, -coef, F);
     }
+  }
+  return fail(WD_ERR_ARG, "unknown term kind");
+}
+
+int term_force(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params& p, double coef, double* F) {
+  const int f = force_fmt(p);
+  WsGuard w(c);
+  Field b, X;
+  WD_TRY(w.get(WD_F64, &X));
+  switch (t.kind) {
+    case WD_TERM_PLAIN:
+    case WD_TERM_HASENBUSCH:
+      WD_TRY(w.get(WD_F64, &b));
+      if (t.kind == WD_TERM_PLAIN) WD_TRY(convert(c, phi, b));
+      else WD_TRY(mhat(c, t.kappa_h, true, phi, b));
+      WD_TRY(solve(c, t.kappa, nullptr, b, X, p));
+      return term_force_xy(c, t, phi, &X, nullptr, f, coef, F);
+    case WD_TERM_POLY:
+      return term_force_xy(c, t, phi, nullptr, nullptr, f, coef, F);
+    case WD_TERM_FILTERED:
+      WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
+      return term_force_xy(c, t, phi, &X, nullptr, f, coef, F);
   }
   return fail(WD_ERR_ARG, "unknown term kind");
 }
@@ -408,6 +433,29 @@ int pf_action(wd_ctx* c, const wd_term* term, const double* phi, const wd_cg_par
   WD_TRY(check_cg(p));
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
   return term_action(c, *term, wrap_f64(c, phi), *p, S);
+}
+
+int pf_action_xy(wd_ctx* c, const wd_term* term, const double* phi, const wd_cg_params* p, double* S,
+                 double* X, double* Y) {
+  if (!c || !phi || !S) return fail(WD_ERR_ARG, "null argument");
+  WD_TRY(check_term(term));
+  WD_TRY(check_cg(p));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  if ((X && (X == phi || X == Y)) || (Y && Y == phi)) return fail(WD_ERR_ARG, "phi, X and Y must differ");
+  Field fx = wrap_f64(c, X), fy = wrap_f64(c, Y);
+  return term_action(c, *term, wrap_f64(c, phi), *p, S, X ? &fx : nullptr, Y ? &fy : nullptr);
+}
+
+int fermion_force_xy(wd_ctx* c, const wd_term* term, const double* phi, const double* X, const double* Y,
+                     int prec, double coef, double* F) {
+  if (!c || !phi || !F) return fail(WD_ERR_ARG, "null argument");
+  WD_TRY(check_term(term));
+  if (prec != WD_F64 && prec != WD_F32) return fail(WD_ERR_ARG, "fermion_force_xy: prec must be FP64 or FP32");
+  if (term->kind != WD_TERM_POLY && !X) return fail(WD_ERR_ARG, "fermion_force_xy: X is required for this term");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  Field fx = wrap_f64(c, X), fy = wrap_f64(c, Y);
+  const bool useY = Y != nullptr && (term->kind == WD_TERM_PLAIN || term->kind == WD_TERM_HASENBUSCH);
+  return term_force_xy(c, *term, wrap_f64(c, phi), X ? &fx : nullptr, useY ? &fy : nullptr, prec, coef, F);
 }
 
 int pf_heatbath(wd_ctx* c, const wd_term* term, const double* chi, const wd_cg_params* p, double* phi) {

@@ -103,6 +103,8 @@ _SIG = {
     "wd_profile_read": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)], _I),
     "wd_launch_count": ([_P, C.POINTER(C.c_longlong)], _I),
     "mdagm_apply_noalloc": ([C.POINTER(C.c_int), _P, _D, _P, _P, _P], _I),
+    "pf_action_xy": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), C.POINTER(_D), _P, _P], _I),
+    "fermion_force_xy": ([_P, C.POINTER(wd_term), _P, _P, _P, _I, _D, _P], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -254,6 +256,14 @@ class Lattice:
         S = C.c_double(0)
         _check(lib.pf_action(self.h, C.byref(t), _ptr(phi), C.byref(params), C.byref(S)))
         return S.value
+
+    def pf_action_xy(self, t, phi, params, X=None, Y=None):
+        S = C.c_double(0)
+        _check(lib.pf_action_xy(self.h, C.byref(t), _ptr(phi), C.byref(params), C.byref(S), _ptr(X), _ptr(Y)))
+        return S.value
+
+    def fermion_force_xy(self, t, phi, X, Y, prec, coef, F):
+        _check(lib.fermion_force_xy(self.h, C.byref(t), _ptr(phi), _ptr(X), _ptr(Y), prec, coef, _ptr(F)))
 
     def pf_heatbath(self, t, chi, params, phi):
         _check(lib.pf_heatbath(self.h, C.byref(t), _ptr(chi), C.byref(params), _ptr(phi)))
