@@ -45,6 +45,9 @@ DEFAULT_WORKLOAD = "c5_32x32x32x64"
 # Integrator levels, outermost first: (group, steps per enclosing T).
 # group 0: filtered + Hasenbusch terms, group 1: P(J) term, -1: gauge action.
 LEVELS = [(0, 10), (1, 1), (-1, 2)]
+# Residual recomputation of the mixed-precision solves: 1 = double-float
+# (2 x FP32, about 48 bits, on the FP32 pipes), 0 = FP64.
+RESIDUAL_MODE = 1
 # K_hat applications of one trajectory of the default workload, counted by
 # the library's N_mat counter (algorithmic count; the reference arm scales
 # its per-K_hat time by it).
@@ -224,6 +227,7 @@ def main():
     U_host = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
     lat = wd.Lattice(dims)
     lat.wd_set_recon(wd.RECON_12)
+    lat.wd_set_residual(RESIDUAL_MODE)
     U_dev = U_host.to("cuda", non_blocking=True)
     lat.wd_gauge_load(U_dev)
     terms = [wd.term(wd.POLY, w["kappa_h"], poly=w["poly"]), wd.term(wd.FILTERED, w["kappa_h"], poly=w["poly"]),
@@ -312,7 +316,10 @@ def main():
         b = lat.half_spinor()
         lat.wd_apply(w["kappa"], True, wd.F64, chi, b)
         F = lat.algebra_field()
-        for name, prec in (("fp64", wd.F64), ("mixed_fp32", wd.F32), ("mixed_bf16", wd.BF16)):
+        runs = (("fp64", wd.F64, 0), ("mixed_fp32_fp64resid", wd.F32, 0), ("mixed_fp32", wd.F32, RESIDUAL_MODE),
+                ("mixed_bf16", wd.BF16, RESIDUAL_MODE))
+        for name, prec, rmode in runs:
+            lat.wd_set_residual(rmode)
             x = lat.half_spinor()
             torch.cuda.synchronize()
             t = time.perf_counter()
@@ -321,16 +328,26 @@ def main():
             extras[f"cg_{name}"] = {"s": time.perf_counter() - t, "iters": info["iters"],
                                     "reliable_updates": info["reliable_updates"],
                                     "true_rel_resid": info["true_rel_resid"]}
-            if name != "mixed_bf16":
+            if name in ("fp64", "mixed_fp32"):
                 torch.cuda.synchronize()
                 t = time.perf_counter()
                 lat.fermion_force(terms[2], chi, wd.cg_params(tol=1e-10, prec=prec), 1.0, F)
                 torch.cuda.synchronize()
                 extras[f"force_hasenbusch_{name}"] = {"s": time.perf_counter() - t}
+            # the filtered term's solve: the FP64-residual cost centre
+            if name in ("mixed_fp32_fp64resid", "mixed_fp32"):
+                x = lat.half_spinor()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                info = lat.cg_solve(w["kappa_h"], b, x, wd.cg_params(tol=1e-10, prec=prec), filt=w["poly"])
+                torch.cuda.synchronize()
+                extras[f"filtered_cg_{name}"] = {"s": time.perf_counter() - t, "iters": info["iters"],
+                                                 "true_rel_resid": info["true_rel_resid"]}
+        lat.wd_set_residual(RESIDUAL_MODE)
         # stand-alone K_hat bandwidth per precision (10 applications each)
         out = lat.half_spinor()
-        for name, prec, recon in (("fp64", wd.F64, 0), ("fp32", wd.F32, 0), ("fp32_recon12", wd.F32, 1),
-                                  ("bf16_recon12", wd.BF16, 1)):
+        for name, prec, recon in (("fp64", wd.F64, 0), ("double_float", wd.DF, 0), ("fp32", wd.F32, 0),
+                                  ("fp32_recon12", wd.F32, 1), ("bf16_recon12", wd.BF16, 1)):
             lat.wd_set_recon(recon)
             lat.wd_profile_enable(1)
             lat.mdagm_apply(w["kappa"], prec, 1, chi, out)
@@ -356,7 +373,10 @@ def main():
                 "config": {"workload": args.workload, "dims": list(dims), "kappa": w["kappa"],
                            "kappa_h": w["kappa_h"], "poly": list(w["poly"]), "beta": w["beta"],
                            "integrator": "nested Omelyan 2MN", "levels": LEVELS, "tau": w["tau"],
-                           "action": "PF-MP + Wilson gauge", "precision": "FP32 bulk, FP64 reliable updates",
+                           "action": "PF-MP + Wilson gauge",
+                           "precision": "FP32 bulk (12-real links); reliable updates with b, x, r, dots in FP64 and "
+                                        + ("A x in double-float (2xFP32, ~48 bits)" if RESIDUAL_MODE else "A x in FP64")
+                                        + "; links, momenta, H in FP64",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "working set (1.2 GB FP64 links + FP32 copies) far above the 126 MB L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

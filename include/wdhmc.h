@@ -64,8 +64,10 @@ enum wd_status_code {
   WD_ERR_STATE = 5     /* call made before the state it needs (e.g. no gauge field) */
 };
 
-/* Arithmetic used inside an operator application or for the bulk of a solve. */
-enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3 };
+/* Arithmetic used inside an operator application or for the bulk of a solve.
+ * WD_DF (operator calls wd_hop / wd_apply / mdagm_apply only): double-float,
+ * two FP32 words per real with error-free FP32 arithmetic, about 48 bits. */
+enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3, WD_DF = 4 };
 
 /* Storage of the low-precision links: 18 reals, or 12 with the third row
  * rebuilt as (r0 x r1)^* (SU(3)); the antiperiodic sign is never folded in. */
@@ -118,6 +120,14 @@ int wd_context_destroy(wd_ctx* ctx);
 const char* wd_last_error(void);
 /* Low-precision link storage (enum wd_recon); takes effect at the next load. */
 int wd_set_recon(wd_ctx* ctx, int recon);
+/* Arithmetic of the residual recomputation r = b - A x inside mixed-precision
+ * solves (the reliable updates): mode 0 = FP64 (default); mode 1 =
+ * double-float, x split into two FP32 words and A applied with error-free
+ * FP32 arithmetic (about 48 significant bits, 1e-14 relative; b, x, r, dots
+ * stay FP64).  GB300 runs FP64 at 1/60 of its FP32 rate, and a filtered
+ * operator's residual costs n+1 K_hat.  Mode 1 allocates a double-float copy
+ * of the links (as much as the FP64 copy) on first use. */
+int wd_set_residual(wd_ctx* ctx, int mode);
 /* Volume helpers: out[0] = V, out[1] = Vh. */
 int wd_volume(const wd_ctx* ctx, long long out[2]);
 

@@ -67,8 +67,19 @@ using namespace wd;
 #define CHECK_PTR(p) \
   if ((p) == nullptr) return fail(WD_ERR_ARG, #p " is null")
 
-static int check_prec(int prec) {
-  if (prec < WD_F64 || prec > WD_BF16) return fail(WD_ERR_ARG, "unknown precision");
+static_assert((int)WD_DF == (int)WD_DD, "the public double-float precision is the internal format");
+
+static int ensure_gauge_dd(wd_ctx* c) {
+  if (c->gauge_dd != nullptr) return WD_OK;
+  WD_CUDA(cudaMalloc(&c->gauge_dd, sizeof(float4) * 72 * c->g.Vh));
+  if (c->have_gauge) return gauge_lowprec_k(c);
+  return WD_OK;
+}
+
+// operator entry points accept every precision including double-float
+static int check_prec(wd_ctx* c, int prec) {
+  if (prec < WD_F64 || prec > WD_DF) return fail(WD_ERR_ARG, "unknown precision");
+  if (prec == WD_DF) return ensure_gauge_dd(c);
   return WD_OK;
 }
 
@@ -120,6 +131,7 @@ int wd_context_destroy(wd_ctx* c) {
   cudaFree(c->gauge64);
   cudaFree(c->gauge32);
   cudaFree(c->gauge32r12);
+  cudaFree(c->gauge_dd);
   cudaFree(c->red_partial);
   cudaFree(c->red_counter);
   cudaFree(c->red_out);
@@ -141,6 +153,14 @@ int wd_set_recon(wd_ctx* c, int recon) {
   CHECK_CTX(c);
   if (recon != WD_RECON_18 && recon != WD_RECON_12) return fail(WD_ERR_ARG, "recon must be 18 or 12");
   c->recon = recon;
+  return WD_OK;
+}
+
+int wd_set_residual(wd_ctx* c, int mode) {
+  CHECK_CTX(c);
+  if (mode != 0 && mode != 1) return fail(WD_ERR_ARG, "mode must be 0 (FP64) or 1 (double-float)");
+  if (mode == 1) WD_TRY(ensure_gauge_dd(c));
+  c->resid_dd = mode;
   return WD_OK;
 }
 
@@ -202,8 +222,9 @@ int wd_hop(wd_ctx* c, int out_parity, int dagger, int prec, const double* in, do
   CHECK_CTX(c);
   CHECK_PTR(in);
   CHECK_PTR(out);
-  WD_TRY(check_prec(prec));
   if (out_parity != 0 && out_parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  WD_TRY(check_prec(c, prec));
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
   Field fi = wrap_f64(c, in), fo = wrap_f64(c, out);
   if (prec == WD_F64) return hop(c, out_parity, dagger != 0, fi, fo, nullptr, 0.0, false, false);
@@ -220,8 +241,8 @@ int wd_apply(wd_ctx* c, double kappa, int dagger, int prec, const double* in, do
   CHECK_CTX(c);
   CHECK_PTR(in);
   CHECK_PTR(out);
-  WD_TRY(check_prec(prec));
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  WD_TRY(check_prec(c, prec));
   Field fi = wrap_f64(c, in), fo = wrap_f64(c, out);
   WsGuard w(c);
   Field t, a, b;
@@ -238,16 +259,17 @@ int mdagm_apply(wd_ctx* c, double kappa, int prec, int nrhs, const double* in, d
   CHECK_CTX(c);
   CHECK_PTR(in);
   CHECK_PTR(out);
-  WD_TRY(check_prec(prec));
   if (nrhs < 1) return fail(WD_ERR_ARG, "nrhs must be >= 1");
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  WD_TRY(check_prec(c, prec));
   WsGuard w(c);
   Field t1, t2, a, b;
   WD_TRY(w.get(prec, &t1));
   WD_TRY(w.get(prec, &t2));
   if (prec != WD_F64) {
     WD_TRY(w.get(prec, &a));
-    WD_TRY(w.get(prec == WD_F64 ? WD_F64 : (prec == WD_F32 ? WD_F32 : WD_F32), &b));
+    // K_hat of 16-bit input writes FP32; FP32 and double-float keep their format
+    WD_TRY(w.get(prec == WD_DF ? WD_DD : WD_F32, &b));
   }
   const long stride = 24 * c->g.Vh;
   for (int k = 0; k < nrhs; ++k) {
@@ -276,7 +298,7 @@ int wd_profile_enable(wd_ctx* c, int every_n) {
   Prof& p = c->prof;
   p.every = every_n;
   p.seen = 0;
-  for (int f = 0; f < 4; ++f) { p.launches[f] = 0; p.ms[f] = 0.0; p.bytes[f] = 0.0; }
+  for (int f = 0; f < Prof::NF; ++f) { p.launches[f] = 0; p.ms[f] = 0.0; p.bytes[f] = 0.0; }
   for (auto& e : p.ev) cudaEventDestroy(e);
   p.ev.clear();
   p.ev_bytes.clear();
@@ -286,7 +308,7 @@ int wd_profile_enable(wd_ctx* c, int every_n) {
 
 int wd_profile_read(wd_ctx* c, int fmt, long long* launches, double* total_ms, double* bytes) {
   CHECK_CTX(c);
-  if (fmt < -1 || fmt > WD_BF16) return fail(WD_ERR_ARG, "fmt must be -1 (all) or a wd_prec");
+  if (fmt < -1 || fmt >= Prof::NF) return fail(WD_ERR_ARG, "fmt must be -1 (all), a wd_prec or 4 (double-float)");
   Prof& p = c->prof;
   for (size_t k = 0; k + 1 < p.ev.size(); k += 2) {
     float ms = 0.f;
@@ -304,7 +326,7 @@ int wd_profile_read(wd_ctx* c, int fmt, long long* launches, double* total_ms, d
   p.ev_fmt.clear();
   long long n = 0;
   double ms = 0, b = 0;
-  for (int f = 0; f < 4; ++f) {
+  for (int f = 0; f < Prof::NF; ++f) {
     if (fmt >= 0 && f != fmt) continue;
     n += p.launches[f];
     ms += p.ms[f];

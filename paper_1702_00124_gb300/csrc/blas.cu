@@ -12,7 +12,8 @@ constexpr int BL_THREADS = 256;
 
 size_t field_bytes(int fmt, long Vh) {
   switch (fmt) {
-    case WD_F64: return (size_t)Vh * 24 * 8;
+    case WD_F64:
+    case WD_DD: return (size_t)Vh * 24 * 8;
     case WD_F32: return (size_t)Vh * 24 * 4;
     default: return (size_t)Vh * 24 * 2;   // the norm array is separate
   }
@@ -25,12 +26,18 @@ static int with_fmt(const Field& f, Fn&& fn) {
     case WD_F32: return fn(sp32(f));
     case WD_F16: return fn(sp16<__half>(f));
     case WD_BF16: return fn(sp16<__nv_bfloat16>(f));
+    case WD_DD: return fn(spdd(f));
   }
   return fail(WD_ERR_ARG, "unknown field format");
 }
 
+// arithmetic of a kernel on two formats: FP64 when both are FP64, double-float
+// when both are double-float, FP64 for conversions between the two, else FP32
 template <class A, class B> struct Pick { using T = float; };
 template <> struct Pick<SpF64, SpF64> { using T = double; };
+template <> struct Pick<SpDD, SpDD> { using T = dd; };
+template <> struct Pick<SpF64, SpDD> { using T = double; };
+template <> struct Pick<SpDD, SpF64> { using T = double; };
 
 // ---------------------------------------------------------------------------
 template <class T, class In, class Out>
@@ -78,6 +85,7 @@ int caxpby(wd_ctx* c, double ar, double ai, const Field& x, double br, double bi
     F Y = X, O = X;
     if constexpr (std::is_same<F, SpF64>::value) { Y = sp64(y); O = sp64(out); }
     else if constexpr (std::is_same<F, SpF32>::value) { Y = sp32(y); O = sp32(out); }
+    else if constexpr (std::is_same<F, SpDD>::value) { Y = spdd(y); O = spdd(out); }
     else { Y = F{(uint4*)y.data, y.norm, y.stride}; O = F{(uint4*)out.data, out.norm, out.stride}; }
     k_caxpby<T><<<nblocks(n, BL_THREADS), BL_THREADS, 0, c->stream>>>(n, (T)ar, (T)ai, X, (T)br, (T)bi, Y, O);
     WD_CHECK_LAUNCH();
@@ -314,8 +322,11 @@ int poly_step(wd_ctx* c, double a, double mu, double b, const Field& v, const Fi
   } else if (v.fmt == WD_F32) {
     k_poly_step<float><<<nb, BL_THREADS, 0, c->stream>>>(n, (float)a, (float)mu, (float)b, sp32(v), sp32(s),
                                                          sp32(Ks), sp32(sprev), sp32(out));
+  } else if (v.fmt == WD_DD) {
+    k_poly_step<dd><<<nb, BL_THREADS, 0, c->stream>>>(n, dd(a), dd(mu), dd(b), spdd(v), spdd(s), spdd(Ks),
+                                                      spdd(sprev), spdd(out));
   } else {
-    return fail(WD_ERR_ARG, "poly_step: FP64 or FP32 fields only");
+    return fail(WD_ERR_ARG, "poly_step: FP64, FP32 or double-float fields only");
   }
   WD_CHECK_LAUNCH();
   return WD_OK;

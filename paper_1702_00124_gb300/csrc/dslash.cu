@@ -9,7 +9,8 @@ namespace wd {
 
 static int spinor_bytes(int fmt) {
   switch (fmt) {
-    case WD_F64: return 192;
+    case WD_F64:
+    case WD_DD: return 192;
     case WD_F32: return 96;
     default: return 52;   // 48 bytes of 16-bit values + 4-byte norm
   }
@@ -23,7 +24,7 @@ double hop_bytes(int fmt_in, int fmt_out, bool xpay, int gauge_bytes_per_link, l
 }
 
 static int gauge_link_bytes(wd_ctx* c, int fmt_in) {
-  if (fmt_in == WD_F64) return 144;
+  if (fmt_in == WD_F64 || fmt_in == WD_DD) return 144;
   return c->recon == WD_RECON_12 ? 48 : 72;
 }
 
@@ -60,6 +61,7 @@ int hop(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, con
   int s;
   if (in.fmt == WD_F64) s = hop_f64(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   else if (in.fmt == WD_F32) s = hop_f32(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
+  else if (in.fmt == WD_DD) s = hop_dd(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   else s = hop_h16(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);
   if (s != WD_OK) return s;
   prof_end(c, e0, hop_bytes(in.fmt, out.fmt, y != nullptr, gauge_link_bytes(c, in.fmt), c->g.Vh), in.fmt);

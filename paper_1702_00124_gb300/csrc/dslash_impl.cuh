@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(HopArgs<In, Out, Y, G> a) {
     }
     if constexpr (NORM) {
 #pragma unroll
-      for (int j = 0; j < 12; ++j) part[0] += (double)acc[j].r * acc[j].r + (double)acc[j].i * acc[j].i;
+      for (int j = 0; j < 12; ++j) {
+        const double re = (double)acc[j].r, im = (double)acc[j].i;
+        part[0] += re * re + im * im;
+      }
     }
     a.out.store(cb, acc);
   }
@@ -179,6 +182,11 @@ int hop_with_gauge(wd_ctx* c, int out_par, bool dag, In in, Out out, Y y, bool x
                    bool norm_cg, bool in_cg, bool use64) {
   Reduce red = reducer(c);
   CGState* st = (norm_cg || in_cg) ? c->cgs : nullptr;
+  if constexpr (std::is_same<T, dd>::value) {
+    GDD G{c->gauge_dd, c->g.Vh};
+    HopArgs<In, Out, Y, GDD> a{c->g, out_par, in, out, y, G, alpha, red, st};
+    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+  } else {
   if (use64) {
     GF64 G{c->gauge64, c->g.Vh};
     HopArgs<In, Out, Y, GF64> a{c->g, out_par, in, out, y, G, alpha, red, st};
@@ -192,6 +200,7 @@ int hop_with_gauge(wd_ctx* c, int out_par, bool dag, In in, Out out, Y y, bool x
   GF32 G{c->gauge32, c->g.Vh};
   HopArgs<In, Out, Y, GF32> a{c->g, out_par, in, out, y, G, alpha, red, st};
   return launch_hop<T>(c, dag, xpay, norm_cg, a);
+  }
 }
 
 // per-family dispatchers (one translation unit each)
@@ -201,5 +210,8 @@ int hop_f32(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out,
             double alpha, bool norm_cg, bool in_cg);
 int hop_h16(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
             double alpha, bool norm_cg, bool in_cg);
+int hop_dd(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, const Field* y,
+           double alpha, bool norm_cg, bool in_cg);
+inline SpDD spdd(const Field& f) { return SpDD{(float4*)f.data, f.stride}; }
 
 }  // namespace wd

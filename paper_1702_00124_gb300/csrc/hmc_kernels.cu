@@ -116,7 +116,7 @@ __device__ __forceinline__ void alg_matrix(const double (&p)[8], double s, cpx<d
 }
 
 __global__ void __launch_bounds__(H_THREADS) k_step_T(Geom g, const double* P, double eps, double2* U64,
-                                                      float2* U32, float4* U12) {
+                                                      float2* U32, float4* U12, float4* Udd) {
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= 8 * g.Vh) return;
   const long cb = tid % g.Vh;
@@ -144,12 +144,20 @@ __global__ void __launch_bounds__(H_THREADS) k_step_T(Geom g, const double* P, d
 #pragma unroll
   for (int j = 0; j < 3; ++j)
     v12[j * g.Vh] = make_float4((float)V[2 * j].r, (float)V[2 * j].i, (float)V[2 * j + 1].r, (float)V[2 * j + 1].i);
+  if (Udd != nullptr) {
+    float4* vd = Udd + (long)mp * 9 * g.Vh + cb;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const dd r(V[j].r), m(V[j].i);
+      vd[j * g.Vh] = make_float4(r.hi, r.lo, m.hi, m.lo);
+    }
+  }
 }
 
 int step_T_k(wd_ctx* c, const double* P, double eps) {
   const long n = 8 * c->g.Vh;
   k_step_T<<<nblocks(n, H_THREADS), H_THREADS, 0, c->stream>>>(c->g, P, eps, c->gauge64, c->gauge32,
-                                                                c->gauge32r12);
+                                                                c->gauge32r12, c->gauge_dd);
   WD_CHECK_LAUNCH();
   return WD_OK;
 }

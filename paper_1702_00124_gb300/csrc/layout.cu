@@ -44,7 +44,7 @@ int pack_k(wd_ctx* c, bool unpack, int nouter, int nchunk, int chunk, int parity
   return WD_OK;
 }
 
-__global__ void k_gauge_lowprec(long n9, long Vh, const double2* U64, float2* U32, float4* U12) {
+__global__ void k_gauge_lowprec(long n9, long Vh, const double2* U64, float2* U32, float4* U12, float4* Udd) {
   // one thread per link (mu, parity, cb): n = 8 Vh
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n9) return;
@@ -53,6 +53,14 @@ __global__ void k_gauge_lowprec(long n9, long Vh, const double2* U64, float2* U3
   double2 v[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) v[j] = u[j * Vh];
+  if (Udd != nullptr) {
+    float4* o = Udd + mp * 9 * Vh + cb;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const dd r(v[j].x), m(v[j].y);
+      o[j * Vh] = make_float4(r.hi, r.lo, m.hi, m.lo);
+    }
+  }
   float2* o = U32 + mp * 9 * Vh + cb;
 #pragma unroll
   for (int j = 0; j < 9; ++j) o[j * Vh] = make_float2((float)v[j].x, (float)v[j].y);
@@ -64,7 +72,8 @@ __global__ void k_gauge_lowprec(long n9, long Vh, const double2* U64, float2* U3
 
 int gauge_lowprec_k(wd_ctx* c) {
   const long n = 8 * c->g.Vh;
-  k_gauge_lowprec<<<nblocks(n, 128), 128, 0, c->stream>>>(n, c->g.Vh, c->gauge64, c->gauge32, c->gauge32r12);
+  k_gauge_lowprec<<<nblocks(n, 128), 128, 0, c->stream>>>(n, c->g.Vh, c->gauge64, c->gauge32, c->gauge32r12,
+                                                          c->gauge_dd);
   WD_CHECK_LAUNCH();
   return WD_OK;
 }

@@ -48,6 +48,49 @@ template <int K, class T> __host__ __device__ __forceinline__ cpx<T> ipow(cpx<T>
 }
 
 // ----------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with two FP32 words (|lo| <=
+// ulp(hi)/2), about 48 significant bits.  Sum and product follow the
+// error-free transformations of Knuth (two-sum) and Dekker (two-product, here
+// with an FMA); they run on the FP32 pipes, which GB300 has 60x more of than
+// FP64.  Used only where an FP64-accurate operator is needed many times: the
+// residual recomputation of mixed-precision solves, when selected.
+struct dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dd(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ explicit dd(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__host__ __device__ __forceinline__ dd dd_fast2sum(float a, float b) {
+  const float s = a + b;
+  return dd(s, b - (s - a));
+}
+__host__ __device__ __forceinline__ dd dd_2sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return dd(s, (a - (s - bb)) + (b - bb));
+}
+__host__ __device__ __forceinline__ dd operator+(dd a, dd b) {
+  dd s = dd_2sum(a.hi, b.hi);
+  const dd t = dd_2sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = dd_fast2sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return dd_fast2sum(s.hi, s.lo);
+}
+__host__ __device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
+__host__ __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__host__ __device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return dd_fast2sum(p, e);
+}
+
+// ----------------------------------------------------------------------------
 // Gamma matrices, DeGrand-Rossi chiral basis (gamma_5 = diag(1,1,-1,-1)).
 // Each gamma_mu has one non-zero per row; row a (a = 0,1) couples to column
 // PERM[mu][a] with value i^PH[mu][a]:
@@ -177,6 +220,38 @@ template <class H> struct Sp16 {
   }
 };
 
+// Double-float spinor: float4 [12][Vh], component j = (re.hi, re.lo, im.hi, im.lo);
+// 16 bytes per complex like FP64.  Internal format id WD_DD.
+constexpr int WD_DD = 4;
+template <class T> __device__ __forceinline__ T dd_to(dd v);
+template <> __device__ __forceinline__ dd dd_to<dd>(dd v) { return v; }
+template <> __device__ __forceinline__ double dd_to<double>(dd v) { return (double)v; }
+template <> __device__ __forceinline__ float dd_to<float>(dd v) { return v.hi + v.lo; }
+template <class T> __device__ __forceinline__ dd to_dd(T v) { return dd((double)v); }
+template <> __device__ __forceinline__ dd to_dd<dd>(dd v) { return v; }
+template <> __device__ __forceinline__ dd to_dd<float>(float v) { return dd(v, 0.f); }
+
+struct SpDD {
+  using real = dd;
+  static constexpr int fmt = WD_DD;
+  float4* p;
+  long stride;
+  template <class T> __device__ __forceinline__ void loadT(long i, cpx<T> (&s)[12]) const {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const float4 v = __ldg(p + j * stride + i);
+      s[j] = {dd_to<T>(dd(v.x, v.y)), dd_to<T>(dd(v.z, v.w))};
+    }
+  }
+  template <class T> __device__ __forceinline__ void store(long i, const cpx<T> (&s)[12]) const {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const dd r = to_dd(s[j].r), m = to_dd(s[j].i);
+      p[j * stride + i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+    }
+  }
+};
+
 // ----------------------------------------------------------------------------
 // gauge storage formats; load U_mu(x) for site cb of parity par
 struct GF64 {
@@ -197,6 +272,20 @@ struct GF32 {
     const float2* q = p + ((long)(mu * 2 + par) * 9) * stride + i;
 #pragma unroll
     for (int j = 0; j < 9; ++j) { float2 v = __ldg(q + j * stride); U[j] = {(T)v.x, (T)v.y}; }
+  }
+};
+// double-float links: float4 [4][2][9][Vh], entry = (re.hi, re.lo, im.hi, im.lo)
+struct GDD {
+  using real = dd;
+  const float4* p;
+  long stride;
+  template <class T> __device__ __forceinline__ void load(int mu, int par, long i, cpx<T> (&U)[9]) const {
+    const float4* q = p + ((long)(mu * 2 + par) * 9) * stride + i;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const float4 v = __ldg(q + j * stride);
+      U[j] = {dd_to<T>(dd(v.x, v.y)), dd_to<T>(dd(v.z, v.w))};
+    }
   }
 };
 struct GF32R12 {
@@ -317,9 +406,10 @@ size_t field_bytes(int fmt, long Vh);
 struct Prof {
   int every = 0;
   long long seen = 0;
-  long long launches[4] = {0, 0, 0, 0};
-  double ms[4] = {0, 0, 0, 0};
-  double bytes[4] = {0, 0, 0, 0};
+  static constexpr int NF = 5;      // FP64, FP32, FP16, BF16, double-float
+  long long launches[NF] = {0, 0, 0, 0, 0};
+  double ms[NF] = {0, 0, 0, 0, 0};
+  double bytes[NF] = {0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev;   // pairs, pending
   std::vector<double> ev_bytes;
   std::vector<int> ev_fmt;
@@ -338,6 +428,8 @@ struct wd_ctx {
   double2* gauge64 = nullptr;       // [4][2][9][Vh]
   float2* gauge32 = nullptr;        // [4][2][9][Vh]
   float4* gauge32r12 = nullptr;     // [4][2][3][Vh]
+  float4* gauge_dd = nullptr;       // double-float copy [4][2][9][Vh] (on demand)
+  int resid_dd = 0;                 // residual recomputation in double-float
   double2* gauge_backup = nullptr;  // FP64 links at the start of a trajectory
   double* mom = nullptr;            // momenta of a trajectory [4][2][8][Vh]
   // reduction scratch

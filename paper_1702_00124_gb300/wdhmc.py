@@ -17,7 +17,7 @@ if not os.path.exists(_LIB_PATH):
     raise ImportError(f"libwdhmc.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
 lib = C.CDLL(_LIB_PATH)
 
-F64, F32, F16, BF16 = 0, 1, 2, 3
+F64, F32, F16, BF16, DF = 0, 1, 2, 3, 4   # DF: double-float (operator calls only)
 RECON_18, RECON_12 = 0, 1
 PLAIN, HASENBUSCH, POLY, FILTERED = 0, 1, 2, 3
 ERRORS = {1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_NOCONV", 4: "WD_ERR_NAN", 5: "WD_ERR_STATE"}
@@ -105,6 +105,7 @@ _SIG = {
     "mdagm_apply_noalloc": ([C.POINTER(C.c_int), _P, _D, _P, _P, _P], _I),
     "pf_action_xy": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), C.POINTER(_D), _P, _P], _I),
     "fermion_force_xy": ([_P, C.POINTER(wd_term), _P, _P, _P, _I, _D, _P], _I),
+    "wd_set_residual": ([_P, _I], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -214,6 +215,9 @@ class Lattice:
     # ---- entry points ----------------------------------------------------
     def wd_set_recon(self, recon):
         _check(lib.wd_set_recon(self.h, recon))
+
+    def wd_set_residual(self, mode):
+        _check(lib.wd_set_residual(self.h, mode))
 
     def wd_gauge_load(self, U_lex):
         _check(lib.wd_gauge_load(self.h, _ptr(U_lex)))

@@ -2,7 +2,7 @@
 
 Tolerances (per-site relative error |d(x)| / max(|ref(x)|, 1e-3 rms|ref|)):
 FP64 1e-12, FP32 1e-5, FP16 with per-site norm 3e-3, BF16 with per-site norm
-3e-2.  Lattices: 2^4 (x+mu = x-mu), 4^4, 6x4x6x10 (Vh = 720, a ragged last
+3e-2, double-float (two FP32 words, error-free arithmetic) 1e-12.  Lattices: 2^4 (x+mu = x-mu), 4^4, 6x4x6x10 (Vh = 720, a ragged last
 block of 128 threads), 8^3x16.
 """
 import numpy as np
@@ -13,7 +13,7 @@ from paper_1702_00124_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5, 2: 3e-3, 3: 3e-2}
+TOL = {0: 1e-12, 1: 1e-5, 2: 3e-3, 3: 3e-2, 4: 1e-12}   # 4: double-float
 LATS = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 6, 10), (8, 8, 8, 16)]
 
 
@@ -42,7 +42,7 @@ def test_pack_roundtrip(setup):
     assert np.array_equal(gu.host_c(Ub, U.shape), U)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_hop(setup, prec, dagger):
     dims, U, psi, lat, gu, wd = setup
@@ -56,7 +56,7 @@ def test_hop(setup, prec, dagger):
         assert gu.site_rel_err(got, ref, out_par, dims) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_mhat(setup, prec, dagger):
     dims, U, psi, lat, gu, wd = setup
@@ -69,7 +69,7 @@ def test_mhat(setup, prec, dagger):
     assert gu.site_rel_err(gu.unpack(lat, out, 0), ref, 0, dims) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_khat(setup, prec):
     dims, U, psi, lat, gu, wd = setup
     k = 0.12

@@ -107,6 +107,29 @@ def test_poly_filter_apply(setup, poly, prec):
     assert gu.site_rel_err(gu.unpack(lat, out, 0), ref, 0, s["dims"]) < tol
 
 
+@pytest.mark.parametrize("filt", [None, (8, 0.02, 6.0)], ids=["khat", "filtered"])
+def test_double_float_residual(setup, filt):
+    """Reliable updates with the residual formed in double-float still deliver
+    the FP64 true residual (recomputed here by the oracle's FP64 operator)."""
+    s = setup
+    lat, gu, wd = s["lat"], s["gu"], s["wd"]
+    lat.wd_set_residual(1)
+    try:
+        be = gu.pack(lat, s["b"], 0)
+        x = lat.half_spinor()
+        info = lat.cg_solve(s["kappa"], be, x, wd.cg_params(tol=1e-10, prec=1), filt=filt)
+    finally:
+        lat.wd_set_residual(0)
+    xh = gu.unpack(lat, x, 0)
+    if filt is None:
+        Ax = wilson.apply_Khat(s["U"], xh, s["kappa"])
+    else:
+        Ax = filtered_op(s["U"], s["kappa"], ChebyshevFilter(*filt))(xh)
+    true_rel = np.linalg.norm(s["b"] - Ax) / np.linalg.norm(s["b"])
+    assert true_rel <= 1.01e-10, (true_rel, info)
+    assert abs(true_rel - info["true_rel_resid"]) < 1e-12
+
+
 def test_filtered_solve(setup):
     s = setup
     lat, gu, wd = s["lat"], s["gu"], s["wd"]
