@@ -128,6 +128,12 @@ int wd_set_recon(wd_ctx* ctx, int recon);
  * operator's residual costs n+1 K_hat.  Mode 1 allocates a double-float copy
  * of the links (as much as the FP64 copy) on first use. */
 int wd_set_residual(wd_ctx* ctx, int mode);
+/* Launch-shape autotuner of the hop kernels (on by default): the first launch
+ * of each (formats, link storage, dagger, epilogue) outside a queued CG chunk
+ * times the candidate block sizes and register caps on the context stream and
+ * keeps the fastest for the context's volume.  enable: 1 on, 0 off, -1 leave;
+ * *n_tuned (may be NULL) = number of tuned keys. */
+int wd_set_autotune(wd_ctx* ctx, int enable, int* n_tuned);
 /* Volume helpers: out[0] = V, out[1] = Vh. */
 int wd_volume(const wd_ctx* ctx, long long out[2]);
 

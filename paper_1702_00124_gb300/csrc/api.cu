@@ -156,6 +156,14 @@ int wd_set_recon(wd_ctx* c, int recon) {
   return WD_OK;
 }
 
+int wd_set_autotune(wd_ctx* c, int enable, int* n_tuned) {
+  CHECK_CTX(c);
+  if (enable != 0 && enable != 1 && enable != -1) return fail(WD_ERR_ARG, "enable must be 0, 1 or -1 (query)");
+  if (enable >= 0) c->autotune = enable;
+  if (n_tuned) *n_tuned = (int)c->tune.size();
+  return WD_OK;
+}
+
 int wd_set_residual(wd_ctx* c, int mode) {
   CHECK_CTX(c);
   if (mode != 0 && mode != 1) return fail(WD_ERR_ARG, "mode must be 0 (FP64) or 1 (double-float)");

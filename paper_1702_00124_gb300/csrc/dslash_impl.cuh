@@ -11,7 +11,8 @@
 
 namespace wd {
 
-constexpr int HOP_THREADS = 128;
+constexpr int HOP_THREADS = 128;   // default block size
+constexpr int HOP_MAXT = 256;      // largest block size any launch uses
 
 template <int MU, int SG, class T>
 __device__ __forceinline__ void spin_project(const cpx<T> (&s)[12], cpx<T> (&h)[6]) {
@@ -109,8 +110,9 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int par, long cb, const i
   }
 }
 
-template <class T, bool DAG, bool XPAY, bool NORM, class In, class Out, class Y, class G>
-__global__ void __launch_bounds__(HOP_THREADS) k_hop(HopArgs<In, Out, Y, G> a) {
+// MINB > 1 caps the registers (65536 / (256 MINB) per thread) for occupancy.
+template <class T, bool DAG, bool XPAY, bool NORM, int MINB, class In, class Out, class Y, class G>
+__global__ void __launch_bounds__(HOP_MAXT, MINB) k_hop(HopArgs<In, Out, Y, G> a) {
   if (a.st != nullptr && a.st->flag != 0) return;
   const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
@@ -153,23 +155,70 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(HopArgs<In, Out, Y, G> a) {
   }
 }
 
-template <class T, class In, class Out, class Y, class G>
-int launch_hop(wd_ctx* c, bool dag, bool xpay, bool norm, const HopArgs<In, Out, Y, G>& a) {
-  const int nb = nblocks(c->g.Vh, HOP_THREADS);
-  if (norm && nb > RED_MAX_BLOCKS) return fail(WD_ERR_ARG, "lattice too large for one reduction grid");
-#define WD_L(D, X, N) k_hop<T, D, X, N, In, Out, Y, G><<<nb, HOP_THREADS, 0, c->stream>>>(a)
-  if (!dag) {
-    if (!xpay) WD_L(false, false, false);
-    else if (!norm) WD_L(false, true, false);
-    else WD_L(false, true, true);
-  } else {
-    if (!xpay) WD_L(true, false, false);
-    else if (!norm) WD_L(true, true, false);
-    else WD_L(true, true, true);
+// Launch-shape autotuner.  Candidates: block sizes 64/128/256 with the
+// compiler's register choice, and 128/256 with registers capped at 64 for
+// occupancy.  The first launch of a (formats, links, dagger, epilogue,
+// volume) key outside a queued CG chunk times every candidate with CUDA events
+// on the context stream (all candidates compute the same output) and keeps
+// the fastest; the NORM variant reuses the shape of its key.
+struct HopCfg {
+  int threads, minb;
+};
+constexpr HopCfg HOP_CANDIDATES[] = {{128, 1}, {256, 1}, {64, 1}, {128, 4}, {256, 4}};
+constexpr int HOP_NCAND = sizeof(HOP_CANDIDATES) / sizeof(HOP_CANDIDATES[0]);
+
+template <class T, bool D, bool X, bool N, class In, class Out, class Y, class G>
+void hop_launch_cfg(wd_ctx* c, HopCfg cfg, const HopArgs<In, Out, Y, G>& a) {
+  const int nb = nblocks(c->g.Vh, cfg.threads);
+  if (cfg.minb == 4) k_hop<T, D, X, N, 4, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
+  else k_hop<T, D, X, N, 1, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
+}
+
+template <class T, bool D, bool X, bool N, class In, class Out, class Y, class G>
+int hop_dispatch(wd_ctx* c, long long key, bool may_tune, const HopArgs<In, Out, Y, G>& a) {
+  HopCfg cfg = HOP_CANDIDATES[0];
+  auto it = c->tune.find(key);
+  if (it != c->tune.end()) {
+    cfg = HopCfg{it->second.first, it->second.second};
+  } else if (may_tune && c->autotune && !N) {
+    cudaEvent_t e0, e1;
+    WD_CUDA(cudaEventCreate(&e0));
+    WD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int k = 0; k < HOP_NCAND; ++k) {
+      hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);   // warm
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3; ++r) hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);
+      cudaEventRecord(e1, c->stream);
+      WD_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->launches += 4;
+      WD_CUDA(cudaGetLastError());
+      if (ms < best) { best = ms; cfg = HOP_CANDIDATES[k]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune[key] = {cfg.threads, cfg.minb};
   }
-#undef WD_L
+  hop_launch_cfg<T, D, X, N>(c, cfg, a);
   WD_CHECK_LAUNCH();
   return WD_OK;
+}
+
+template <class T, class In, class Out, class Y, class G>
+int launch_hop(wd_ctx* c, bool dag, bool xpay, bool norm, long long key, bool may_tune,
+               const HopArgs<In, Out, Y, G>& a) {
+  if (norm && nblocks(c->g.Vh, 64) > RED_MAX_BLOCKS) return fail(WD_ERR_ARG, "lattice too large for one reduction grid");
+  key = key * 4 + (dag ? 2 : 0) + (xpay ? 1 : 0);
+  if (!dag) {
+    if (!xpay) return hop_dispatch<T, false, false, false>(c, key, may_tune, a);
+    if (!norm) return hop_dispatch<T, false, true, false>(c, key, may_tune, a);
+    return hop_dispatch<T, false, true, true>(c, key, may_tune, a);
+  }
+  if (norm) return fail(WD_ERR_ARG, "hop: the |out|^2 epilogue exists for M_hat, not M_hat^dag");
+  if (!xpay) return hop_dispatch<T, true, false, false>(c, key, may_tune, a);
+  return hop_dispatch<T, true, true, false>(c, key, may_tune, a);
 }
 
 // format objects from fields
@@ -182,24 +231,27 @@ int hop_with_gauge(wd_ctx* c, int out_par, bool dag, In in, Out out, Y y, bool x
                    bool norm_cg, bool in_cg, bool use64) {
   Reduce red = reducer(c);
   CGState* st = (norm_cg || in_cg) ? c->cgs : nullptr;
+  // tuning key: formats of in / out / y and the link storage
+  const long long base = ((long long)In::fmt * 8 + Out::fmt) * 8 + (xpay ? Y::fmt : 7);
+  const bool may_tune = !in_cg;
   if constexpr (std::is_same<T, dd>::value) {
     GDD G{c->gauge_dd, c->g.Vh};
     HopArgs<In, Out, Y, GDD> a{c->g, out_par, in, out, y, G, alpha, red, st};
-    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+    return launch_hop<T>(c, dag, xpay, norm_cg, base * 4 + 3, may_tune, a);
   } else {
   if (use64) {
     GF64 G{c->gauge64, c->g.Vh};
     HopArgs<In, Out, Y, GF64> a{c->g, out_par, in, out, y, G, alpha, red, st};
-    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+    return launch_hop<T>(c, dag, xpay, norm_cg, base * 4 + 0, may_tune, a);
   }
   if (c->recon == WD_RECON_12) {
     GF32R12 G{c->gauge32r12, c->g.Vh};
     HopArgs<In, Out, Y, GF32R12> a{c->g, out_par, in, out, y, G, alpha, red, st};
-    return launch_hop<T>(c, dag, xpay, norm_cg, a);
+    return launch_hop<T>(c, dag, xpay, norm_cg, base * 4 + 2, may_tune, a);
   }
   GF32 G{c->gauge32, c->g.Vh};
   HopArgs<In, Out, Y, GF32> a{c->g, out_par, in, out, y, G, alpha, red, st};
-  return launch_hop<T>(c, dag, xpay, norm_cg, a);
+  return launch_hop<T>(c, dag, xpay, norm_cg, base * 4 + 1, may_tune, a);
   }
 }
 

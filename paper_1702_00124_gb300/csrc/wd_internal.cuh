@@ -19,6 +19,8 @@
 
 #include <string>
 #include <type_traits>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "wdhmc.h"
@@ -444,6 +446,8 @@ struct wd_ctx {
   std::vector<bool> pool_used;
   long long nmat = 0;
   long long launches = 0;           // kernels launched by the library
+  int autotune = 1;                 // time launch shapes on first use
+  std::unordered_map<long long, std::pair<int, int>> tune;   // key -> (threads, minb)
   wd::Prof prof;
 };
 

@@ -106,6 +106,7 @@ _SIG = {
     "pf_action_xy": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), C.POINTER(_D), _P, _P], _I),
     "fermion_force_xy": ([_P, C.POINTER(wd_term), _P, _P, _P, _I, _D, _P], _I),
     "wd_set_residual": ([_P, _I], _I),
+    "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -218,6 +219,11 @@ class Lattice:
 
     def wd_set_residual(self, mode):
         _check(lib.wd_set_residual(self.h, mode))
+
+    def wd_set_autotune(self, enable=-1):
+        n = C.c_int(0)
+        _check(lib.wd_set_autotune(self.h, enable, C.byref(n)))
+        return n.value
 
     def wd_gauge_load(self, U_lex):
         _check(lib.wd_gauge_load(self.h, _ptr(U_lex)))
