@@ -385,7 +385,8 @@ def main():
                 "trajectory": {"dH": [float(r["dH"]) for r in timed], "accepted": acc,
                                "n_mat_per_traj": nmat, "force_evals": [r["n_force_evals"] for r in timed],
                                "integrator_ops": len(ops)},
-                "breakdown": extras}
+                "breakdown": extras,
+                "autotuned_hop_shapes": {str(k): list(v) for k, v in lat.tuned().items()}}
         print(json.dumps(line))
     lat.close()
     if dist:

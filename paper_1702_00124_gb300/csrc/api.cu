@@ -164,6 +164,17 @@ int wd_set_autotune(wd_ctx* c, int enable, int* n_tuned) {
   return WD_OK;
 }
 
+int wd_tune_entry(wd_ctx* c, int index, long long* key, int* threads, int* minb) {
+  CHECK_CTX(c);
+  if (index < 0 || index >= (int)c->tune.size()) return fail(WD_ERR_ARG, "index out of range");
+  auto it = c->tune.begin();
+  std::advance(it, index);
+  if (key) *key = it->first;
+  if (threads) *threads = it->second.first;
+  if (minb) *minb = it->second.second;
+  return WD_OK;
+}
+
 int wd_set_residual(wd_ctx* c, int mode) {
   CHECK_CTX(c);
   if (mode != 0 && mode != 1) return fail(WD_ERR_ARG, "mode must be 0 (FP64) or 1 (double-float)");

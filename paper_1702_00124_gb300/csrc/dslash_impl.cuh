@@ -181,24 +181,36 @@ int hop_dispatch(wd_ctx* c, long long key, bool may_tune, const HopArgs<In, Out,
   if (it != c->tune.end()) {
     cfg = HopCfg{it->second.first, it->second.second};
   } else if (may_tune && c->autotune && !N) {
-    cudaEvent_t e0, e1;
-    WD_CUDA(cudaEventCreate(&e0));
-    WD_CUDA(cudaEventCreate(&e1));
+    // candidates interleaved over several rounds (so that no candidate always
+    // runs after the same neighbour), each timed on its own; a candidate's
+    // score is its best launch
+    constexpr int ROUNDS = 4;
+    cudaEvent_t ev[HOP_NCAND * ROUNDS * 2];
+    for (auto& e : ev) WD_CUDA(cudaEventCreate(&e));
+    for (int k = 0; k < HOP_NCAND; ++k) hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);   // warm
+    for (int r = 0; r < ROUNDS; ++r) {
+      for (int j = 0; j < HOP_NCAND; ++j) {
+        const int k = (j + r) % HOP_NCAND;
+        cudaEventRecord(ev[2 * (r * HOP_NCAND + k)], c->stream);
+        hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);
+        cudaEventRecord(ev[2 * (r * HOP_NCAND + k) + 1], c->stream);
+      }
+    }
+    WD_CUDA(cudaEventSynchronize(ev[HOP_NCAND * ROUNDS * 2 - 1]));
+    WD_CUDA(cudaStreamSynchronize(c->stream));
+    c->launches += HOP_NCAND * (ROUNDS + 1);
+    WD_CUDA(cudaGetLastError());
     float best = 1e30f;
     for (int k = 0; k < HOP_NCAND; ++k) {
-      hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);   // warm
-      cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < 3; ++r) hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);
-      cudaEventRecord(e1, c->stream);
-      WD_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->launches += 4;
-      WD_CUDA(cudaGetLastError());
-      if (ms < best) { best = ms; cfg = HOP_CANDIDATES[k]; }
+      float kbest = 1e30f;
+      for (int r = 0; r < ROUNDS; ++r) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[2 * (r * HOP_NCAND + k)], ev[2 * (r * HOP_NCAND + k) + 1]);
+        kbest = ms < kbest ? ms : kbest;
+      }
+      if (kbest < best) { best = kbest; cfg = HOP_CANDIDATES[k]; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto& e : ev) cudaEventDestroy(e);
     c->tune[key] = {cfg.threads, cfg.minb};
   }
   hop_launch_cfg<T, D, X, N>(c, cfg, a);

@@ -107,6 +107,7 @@ _SIG = {
     "fermion_force_xy": ([_P, C.POINTER(wd_term), _P, _P, _P, _I, _D, _P], _I),
     "wd_set_residual": ([_P, _I], _I),
     "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
+    "wd_tune_entry": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I)], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -224,6 +225,15 @@ class Lattice:
         n = C.c_int(0)
         _check(lib.wd_set_autotune(self.h, enable, C.byref(n)))
         return n.value
+
+    def tuned(self):
+        """{key: (threads, minb)} chosen by the launch-shape autotuner."""
+        out = {}
+        for i in range(self.wd_set_autotune(-1)):
+            k, t, m = C.c_longlong(0), C.c_int(0), C.c_int(0)
+            _check(lib.wd_tune_entry(self.h, i, C.byref(k), C.byref(t), C.byref(m)))
+            out[k.value] = (t.value, m.value)
+        return out
 
     def wd_gauge_load(self, U_lex):
         _check(lib.wd_gauge_load(self.h, _ptr(U_lex)))
