@@ -145,6 +145,8 @@ int wd_context_destroy(wd_ctx* c) {
     if (f.norm) cudaFree(f.norm);
   }
   for (auto& e : c->prof.ev) cudaEventDestroy(e);
+  for (auto& kv : c->tune_samples)
+    for (auto& e : kv.second.ev) cudaEventDestroy(e);
   delete c;
   return WD_OK;
 }

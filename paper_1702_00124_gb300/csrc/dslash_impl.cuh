@@ -174,6 +174,33 @@ void hop_launch_cfg(wd_ctx* c, HopCfg cfg, const HopArgs<In, Out, Y, G>& a) {
   else k_hop<T, D, X, N, 1, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
 }
 
+// Online tuning: the first HOP_NCAND * TUNE_ROUNDS tunable launches of a key
+// are real launches of the pipeline, cycling through the candidates, each
+// bracketed by CUDA events (so every candidate is timed in the data flow it
+// serves: inputs just written by the producing kernel, L2 as in production).
+// When all samples are in, the best time per candidate decides.
+constexpr int TUNE_ROUNDS = 3;
+
+inline int tune_settle(wd_ctx* c, long long key, TuneSamples& s) {
+  WD_CUDA(cudaEventSynchronize(s.ev.back()));
+  float best = 1e30f;
+  int pick = 0;
+  for (int k = 0; k < HOP_NCAND; ++k) {
+    float kbest = 1e30f;
+    for (int r = 0; r < TUNE_ROUNDS; ++r) {
+      const int i = r * HOP_NCAND + k;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]);
+      kbest = ms < kbest ? ms : kbest;
+    }
+    if (kbest < best) { best = kbest; pick = k; }
+  }
+  for (auto& e : s.ev) cudaEventDestroy(e);
+  c->tune_samples.erase(key);
+  c->tune[key] = {HOP_CANDIDATES[pick].threads, HOP_CANDIDATES[pick].minb};
+  return WD_OK;
+}
+
 template <class T, bool D, bool X, bool N, class In, class Out, class Y, class G>
 int hop_dispatch(wd_ctx* c, long long key, bool may_tune, const HopArgs<In, Out, Y, G>& a) {
   HopCfg cfg = HOP_CANDIDATES[0];
@@ -181,37 +208,20 @@ int hop_dispatch(wd_ctx* c, long long key, bool may_tune, const HopArgs<In, Out,
   if (it != c->tune.end()) {
     cfg = HopCfg{it->second.first, it->second.second};
   } else if (may_tune && c->autotune && !N) {
-    // candidates interleaved over several rounds (so that no candidate always
-    // runs after the same neighbour), each timed on its own; a candidate's
-    // score is its best launch
-    constexpr int ROUNDS = 4;
-    cudaEvent_t ev[HOP_NCAND * ROUNDS * 2];
-    for (auto& e : ev) WD_CUDA(cudaEventCreate(&e));
-    for (int k = 0; k < HOP_NCAND; ++k) hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);   // warm
-    for (int r = 0; r < ROUNDS; ++r) {
-      for (int j = 0; j < HOP_NCAND; ++j) {
-        const int k = (j + r) % HOP_NCAND;
-        cudaEventRecord(ev[2 * (r * HOP_NCAND + k)], c->stream);
-        hop_launch_cfg<T, D, X, N>(c, HOP_CANDIDATES[k], a);
-        cudaEventRecord(ev[2 * (r * HOP_NCAND + k) + 1], c->stream);
-      }
-    }
-    WD_CUDA(cudaEventSynchronize(ev[HOP_NCAND * ROUNDS * 2 - 1]));
-    WD_CUDA(cudaStreamSynchronize(c->stream));
-    c->launches += HOP_NCAND * (ROUNDS + 1);
-    WD_CUDA(cudaGetLastError());
-    float best = 1e30f;
-    for (int k = 0; k < HOP_NCAND; ++k) {
-      float kbest = 1e30f;
-      for (int r = 0; r < ROUNDS; ++r) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[2 * (r * HOP_NCAND + k)], ev[2 * (r * HOP_NCAND + k) + 1]);
-        kbest = ms < kbest ? ms : kbest;
-      }
-      if (kbest < best) { best = kbest; cfg = HOP_CANDIDATES[k]; }
-    }
-    for (auto& e : ev) cudaEventDestroy(e);
-    c->tune[key] = {cfg.threads, cfg.minb};
+    TuneSamples& s = c->tune_samples[key];
+    const int i = (int)s.ev.size() / 2;               // sample index: round * NCAND + candidate
+    cfg = HOP_CANDIDATES[i % HOP_NCAND];
+    cudaEvent_t e0, e1;
+    WD_CUDA(cudaEventCreate(&e0));
+    WD_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, c->stream);
+    hop_launch_cfg<T, D, X, N>(c, cfg, a);
+    cudaEventRecord(e1, c->stream);
+    s.ev.push_back(e0);
+    s.ev.push_back(e1);
+    WD_CHECK_LAUNCH();
+    if ((int)s.ev.size() == 2 * HOP_NCAND * TUNE_ROUNDS) WD_TRY(tune_settle(c, key, s));
+    return WD_OK;
   }
   hop_launch_cfg<T, D, X, N>(c, cfg, a);
   WD_CHECK_LAUNCH();

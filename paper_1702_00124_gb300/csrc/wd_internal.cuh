@@ -404,6 +404,11 @@ struct Field {
 
 size_t field_bytes(int fmt, long Vh);
 
+// Timing events of a hop key whose launch shape is being tuned.
+struct TuneSamples {
+  std::vector<cudaEvent_t> ev;   // (start, stop) per sampled launch
+};
+
 // Sampled launch timing of the hop kernels, per input-spinor format.
 struct Prof {
   int every = 0;
@@ -448,6 +453,7 @@ struct wd_ctx {
   long long launches = 0;           // kernels launched by the library
   int autotune = 1;                 // time launch shapes on first use
   std::unordered_map<long long, std::pair<int, int>> tune;   // key -> (threads, minb)
+  std::unordered_map<long long, wd::TuneSamples> tune_samples;   // keys being tuned
   wd::Prof prof;
 };
 
