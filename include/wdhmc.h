@@ -269,6 +269,34 @@ int wd_schedule_nested(int kind, double tau, int nlevels, const int* groups, con
 int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups,
                             const int* nsteps, wd_op* ops, int cap, int* nops);
 
+/* ---- batched solves over many lattices and right-hand sides -------------------
+ * Section 2 of the paper: the pseudofermion terms of a trajectory and, here,
+ * many independent lattices each need solves with K_hat.  A batch groups
+ * contexts (lattices of any even extents, gauge fields loaded, one shared
+ * stream) with a hopping parameter and 1..8 right-hand sides each; every
+ * (lattice, rhs) pair is one system.  The right-hand sides of a lattice are
+ * interleaved in the batch's FP32 fields so one warp reads a site's links
+ * once for all of them, and one launch covers every lattice.  Allocates its
+ * fields (6 FP32 vectors per lattice and rhs) at creation. */
+typedef struct wd_batch wd_batch;
+int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const int* nrhs, wd_batch** out);
+int wd_batch_destroy(wd_batch* b);
+/* out[l] = K_hat in[l] per system, FP32 with FP32 links of the contexts'
+ * storage (12 or 18 reals, from the first context).  in[l], out[l]: nrhs[l]
+ * consecutive FP64 half spinors of lattice l (device). */
+int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
+/* Mixed-precision CG for every system from x = 0: FP32 batched iterations,
+ * FP64 reliable updates per system (through its context) to the FP64 true
+ * residual p->tol.  p->check_every iterations (default 16) run between host
+ * checks, as one captured CUDA graph when use_graph (systems that have
+ * converged return at once inside the graph).  infos: one per system, in
+ * lattice order, or NULL.  The first call times the candidate block sizes of
+ * the batched kernels on K_hat b and keeps the fastest. */
+int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const wd_cg_params* p, int use_graph,
+                wd_cg_info* infos);
+/* Systems, block size chosen by the tuner, kernels launched so far. */
+int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches);
+
 /* ---- allocation-free K_hat ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory: code whose device memory belongs to a host

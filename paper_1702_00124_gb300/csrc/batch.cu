@@ -1,0 +1,642 @@
+// Batched solves: many independent lattices of uneven volume, each with
+// several right-hand sides, advanced together.
+//
+// Every (lattice, right-hand side) pair is one system A_s x_s = b_s with
+// A_s = K_hat(kappa_s) on its lattice (Section 2 of the paper: CG on K).  The
+// right-hand sides of one lattice are interleaved in memory
+// (element (chunk, cb, r) at (chunk * Vh + cb) * nrhs + r), so that the lanes
+// of a warp that work on the nrhs systems of one site read that site's links
+// once: the link bytes per system drop by nrhs.  One launch covers all
+// lattices: every block belongs to one lattice (blocks are laid out lattice
+// after lattice), so per-system sums are formed per block and then added in
+// block order by a second small kernel (deterministic).  CG scalars of every
+// system live on the device; an iteration is eight launches, and a chunk of
+// iterations can be captured once in a CUDA graph and replayed.  The bulk is
+// FP32; the residual of a system is recomputed in FP64 (reliable update,
+// through its lattice's own context) when its iterated residual has dropped by
+// delta or below the tolerance.
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "dslash_impl.cuh"
+
+namespace wd {
+
+constexpr int B_MAXR = 8;   // right-hand sides per lattice
+
+enum BField { BF_P = 0, BF_AP, BF_R, BF_X, BF_T1, BF_T2, BF_N };
+
+struct BLat {
+  Geom g;
+  int nr;          // right-hand sides
+  int sys0;        // first system index
+  int block0;      // first block of this lattice
+  int nblocks;
+  int recon;       // 12 or 18 stored reals
+  double kappa;
+  const float4* g12;
+  const float2* g18;
+  float4* f[BF_N];  // interleaved FP32 half spinors, stride 6 chunks x Vh x nr
+};
+
+// format adaptor: spinor index i of one system -> interleaved element
+struct SpIL {
+  float4* p;
+  long stride;    // Vh * nr
+  int nr, r;
+  template <class T> __device__ __forceinline__ void loadT(long i, cpx<T> (&s)[12]) const {
+    SpF32{p, stride}.loadT(i * nr + r, s);
+  }
+  template <class T> __device__ __forceinline__ void store(long i, const cpx<T> (&s)[12]) const {
+    SpF32{p, stride}.store(i * nr + r, s);
+  }
+};
+
+struct BArgs {
+  const BLat* lats;
+  const int* block_lat;    // block -> lattice
+  CGState* st;             // per system
+  double* partial;         // [block][B_MAXR]
+  int out_par;
+};
+
+__device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& cb, int& r, int& s) {
+  L = a.lats + a.block_lat[blockIdx.x];
+  const long item = (long)(blockIdx.x - L->block0) * blockDim.x + threadIdx.x;
+  if (item >= L->g.Vh * L->nr) return false;
+  cb = item / L->nr;
+  r = (int)(item - cb * L->nr);
+  s = L->sys0 + r;
+  return a.st[s].flag == 0;
+}
+
+__device__ __forceinline__ void b_block_partial(const BArgs& a, double (&v)[B_MAXR]) {
+  __shared__ double sh[B_MAXR * 32];
+  block_sum<B_MAXR>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < B_MAXR; ++k) a.partial[(long)blockIdx.x * B_MAXR + k] = v[k];
+  }
+}
+
+template <bool DAG, bool XPAY, bool NORM, bool R12>
+__global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy) {
+  const BLat* L;
+  long cb;
+  int r, s;
+  double v[B_MAXR];
+#pragma unroll
+  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.0;
+  if (b_locate(a, L, cb, r, s)) {
+    const long stride = L->g.Vh * L->nr;
+    SpIL in{L->f[fin], stride, L->nr, r}, out{L->f[fout], stride, L->nr, r};
+    int c[4];
+    L->g.coords(cb, a.out_par, c);
+    cpx<float> acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = mk<float>(0, 0);
+    if constexpr (R12) {
+      GF32R12 G{L->g12, L->g.Vh};
+      hop_dir<0, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<1, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<2, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<3, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+    } else {
+      GF32 G{L->g18, L->g.Vh};
+      hop_dir<0, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<1, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<2, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      hop_dir<3, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+    }
+    if constexpr (XPAY) {
+      cpx<float> yv[12];
+      SpIL{L->f[fy], stride, L->nr, r}.loadT(cb, yv);
+      const float al = (float)(-L->kappa * L->kappa);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
+    }
+    if constexpr (NORM) {
+      double q = 0.0;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) q += (double)acc[j].r * acc[j].r + (double)acc[j].i * acc[j].i;
+#pragma unroll
+      for (int k = 0; k < B_MAXR; ++k)
+        if (k == r) v[k] = q;
+    }
+    out.store(cb, acc);
+  }
+  if constexpr (NORM) b_block_partial(a, v);
+}
+
+// x += alpha p; r -= alpha Ap; partial |r|^2
+__global__ void __launch_bounds__(256) k_bupdate(BArgs a) {
+  const BLat* L;
+  long cb;
+  int r, s;
+  double v[B_MAXR];
+#pragma unroll
+  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.0;
+  if (b_locate(a, L, cb, r, s)) {
+    const long stride = L->g.Vh * L->nr;
+    const float al = (float)a.st[s].alpha;
+    SpIL X{L->f[BF_X], stride, L->nr, r}, P{L->f[BF_P], stride, L->nr, r};
+    SpIL R{L->f[BF_R], stride, L->nr, r}, AP{L->f[BF_AP], stride, L->nr, r};
+    cpx<float> xv[12], pv[12], rv[12], av[12];
+    X.loadT(cb, xv);
+    P.loadT(cb, pv);
+    R.loadT(cb, rv);
+    AP.loadT(cb, av);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      xv[j] = xv[j] + al * pv[j];
+      rv[j] = rv[j] - al * av[j];
+      q += norm2(rv[j]);
+    }
+    X.store(cb, xv);
+    R.store(cb, rv);
+#pragma unroll
+    for (int k = 0; k < B_MAXR; ++k)
+      if (k == r) v[k] = (double)q;
+  }
+  b_block_partial(a, v);
+}
+
+// p = r + beta p
+__global__ void __launch_bounds__(256) k_bpupdate(BArgs a) {
+  const BLat* L;
+  long cb;
+  int r, s;
+  if (!b_locate(a, L, cb, r, s)) return;
+  const long stride = L->g.Vh * L->nr;
+  const float be = (float)a.st[s].beta;
+  SpIL P{L->f[BF_P], stride, L->nr, r}, R{L->f[BF_R], stride, L->nr, r};
+  cpx<float> pv[12], rv[12];
+  P.loadT(cb, pv);
+  R.loadT(cb, rv);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) pv[j] = rv[j] + be * pv[j];
+  P.store(cb, pv);
+}
+
+// Per-system totals of the block partials, in block order, then the CG
+// scalar step.  mode 0: pAp -> alpha; mode 1: |r|^2 -> beta, flags.
+__global__ void k_breduce(const BLat* lats, int nlat, CGState* st, const double* partial, int mode) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+  while (l < nlat && s >= lats[l].sys0 + lats[l].nr) ++l;
+  if (l >= nlat || s < lats[l].sys0) return;
+  CGState& S = st[s];
+  if (S.flag != 0) return;
+  const BLat& L = lats[l];
+  const int r = s - L.sys0;
+  double tot = 0.0;
+  for (int b = 0; b < L.nblocks; ++b) tot += partial[(long)(L.block0 + b) * B_MAXR + r];
+  if (!isfinite(tot)) { S.flag |= FLAG_NAN; return; }
+  if (mode == 0) {
+    S.pAp = tot;
+    if (!(tot > 0.0)) S.flag |= FLAG_NAN;
+    else S.alpha = S.rr / tot;
+  } else {
+    S.rr_old = S.rr;
+    S.beta = tot / S.rr;
+    S.rr = tot;
+    S.iter += 1;
+    if (tot <= S.upd_rr) S.flag |= FLAG_UPDATE;
+    if (S.iter >= S.maxiter) S.flag |= FLAG_MAXITER;
+  }
+}
+
+// one system's slot of an interleaved field <-> a standard FP64 half spinor
+__global__ void k_slot(long Vh, int nr, int r, float4* il, double2* f64, int dir /*0 get, 1 put, 2 zero*/) {
+  const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= Vh) return;
+  SpIL I{il, Vh * nr, nr, r};
+  cpx<double> s[12];
+  if (dir == 0) {
+    I.loadT(cb, s);
+    SpF64{f64, Vh}.store(cb, s);
+  } else if (dir == 1) {
+    SpF64{f64, Vh}.loadT(cb, s);
+    I.store(cb, s);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) s[j] = mk(0.0, 0.0);
+    I.store(cb, s);
+  }
+}
+
+// p_s = r_s + beta p_s for one system
+__global__ void k_slot_pupdate(long Vh, int nr, int r, float4* p, const float4* rr, float beta) {
+  const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= Vh) return;
+  SpIL P{p, Vh * nr, nr, r}, R{const_cast<float4*>(rr), Vh * nr, nr, r};
+  cpx<float> pv[12], rv[12];
+  P.loadT(cb, pv);
+  R.loadT(cb, rv);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) pv[j] = rv[j] + beta * pv[j];
+  P.store(cb, pv);
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+struct wd_batch {
+  std::vector<wd_ctx*> ctx;
+  std::vector<BLat> lat_h;
+  BLat* lat_d = nullptr;
+  int S = 0;                     // systems
+  int threads = 128;             // block size (autotuned on first use)
+  bool tuned = false;
+  std::vector<int> block_lat_h;
+  int* block_lat_d = nullptr;
+  int nblocks = 0;
+  double* partial = nullptr;
+  CGState* st_d = nullptr;
+  CGState* st_h = nullptr;       // pinned
+  cudaStream_t stream = nullptr; // capture-capable stream
+  bool own_stream = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  long long launches = 0;
+  std::vector<void*> mem;
+};
+
+namespace wd {
+
+static int b_layout(wd_batch* b, int threads) {
+  WD_CUDA(cudaStreamSynchronize(b->stream));   // no launch may still use the old layout
+  b->threads = threads;
+  b->block_lat_h.clear();
+  for (size_t l = 0; l < b->lat_h.size(); ++l) {
+    BLat& L = b->lat_h[l];
+    L.block0 = (int)b->block_lat_h.size();
+    L.nblocks = nblocks(L.g.Vh * L.nr, threads);
+    for (int k = 0; k < L.nblocks; ++k) b->block_lat_h.push_back((int)l);
+  }
+  b->nblocks = (int)b->block_lat_h.size();
+  cudaFree(b->block_lat_d);
+  cudaFree(b->partial);
+  b->block_lat_d = nullptr;
+  b->partial = nullptr;
+  WD_CUDA(cudaMalloc(&b->block_lat_d, sizeof(int) * b->nblocks));
+  WD_CUDA(cudaMalloc(&b->partial, sizeof(double) * B_MAXR * b->nblocks));
+  WD_CUDA(cudaMemcpy(b->block_lat_d, b->block_lat_h.data(), sizeof(int) * b->nblocks, cudaMemcpyHostToDevice));
+  WD_CUDA(cudaMemcpy(b->lat_d, b->lat_h.data(), sizeof(BLat) * b->lat_h.size(), cudaMemcpyHostToDevice));
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return WD_OK;
+}
+
+static BArgs b_args(wd_batch* b, int out_par) {
+  return BArgs{b->lat_d, b->block_lat_d, b->st_d, b->partial, out_par};
+}
+
+static int b_hop(wd_batch* b, int out_par, bool dag, int fin, int fout, int fy, bool norm) {
+  const BArgs a = b_args(b, out_par);
+  const bool r12 = b->lat_h[0].recon == 12;
+#define WD_BH(D, X, N, R) k_bhop<D, X, N, R><<<b->nblocks, b->threads, 0, b->stream>>>(a, fin, fout, fy)
+  if (r12) {
+    if (!dag) {
+      if (fy < 0) WD_BH(false, false, false, true);
+      else if (norm) WD_BH(false, true, true, true);
+      else WD_BH(false, true, false, true);
+    } else {
+      if (fy < 0) WD_BH(true, false, false, true);
+      else WD_BH(true, true, false, true);
+    }
+  } else {
+    if (!dag) {
+      if (fy < 0) WD_BH(false, false, false, false);
+      else if (norm) WD_BH(false, true, true, false);
+      else WD_BH(false, true, false, false);
+    } else {
+      if (fy < 0) WD_BH(true, false, false, false);
+      else WD_BH(true, true, false, false);
+    }
+  }
+#undef WD_BH
+  b->launches += 1;
+  WD_CUDA(cudaGetLastError());
+  return WD_OK;
+}
+
+// out = K_hat in for every system (fields of the batch), with pAp when norm
+static int b_khat(wd_batch* b, int fin, int fout, bool norm) {
+  WD_TRY(b_hop(b, 1, false, fin, BF_T1, -1, false));
+  WD_TRY(b_hop(b, 0, false, BF_T1, BF_T2, fin, norm));
+  if (norm) {
+    k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 0);
+    b->launches += 1;
+  }
+  WD_TRY(b_hop(b, 1, true, BF_T2, BF_T1, -1, false));
+  WD_TRY(b_hop(b, 0, true, BF_T1, fout, BF_T2, false));
+  WD_CUDA(cudaGetLastError());
+  return WD_OK;
+}
+
+static int b_iteration(wd_batch* b) {
+  WD_TRY(b_khat(b, BF_P, BF_AP, true));
+  k_bupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
+  k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 1);
+  k_bpupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
+  b->launches += 3;
+  WD_CUDA(cudaGetLastError());
+  return WD_OK;
+}
+
+static int b_slot(wd_batch* b, int l, int r, int field, double* f64, int dir) {
+  const BLat& L = b->lat_h[l];
+  k_slot<<<nblocks(L.g.Vh, 128), 128, 0, b->stream>>>(L.g.Vh, L.nr, r, L.f[field], (double2*)f64, dir);
+  b->launches += 1;
+  WD_CUDA(cudaGetLastError());
+  return WD_OK;
+}
+
+static int b_enter(wd_batch* b) {   // order the batch stream after the contexts' stream
+  if (!b->own_stream) return WD_OK;
+  WD_CUDA(cudaEventRecord(b->ev_in, b->ctx[0]->stream));
+  WD_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  return WD_OK;
+}
+static int b_leave(wd_batch* b) {
+  if (!b->own_stream) return WD_OK;
+  WD_CUDA(cudaEventRecord(b->ev_out, b->stream));
+  WD_CUDA(cudaStreamWaitEvent(b->ctx[0]->stream, b->ev_out, 0));
+  return WD_OK;
+}
+
+// Time the batched K_hat for each candidate block size; keep the fastest.
+static int b_autotune(wd_batch* b) {
+  const int cand[] = {128, 256, 64};
+  float best = 1e30f;
+  int pick = 128;
+  cudaEvent_t e0, e1;
+  WD_CUDA(cudaEventCreate(&e0));
+  WD_CUDA(cudaEventCreate(&e1));
+  for (int t : cand) {
+    WD_TRY(b_layout(b, t));
+    WD_TRY(b_khat(b, BF_P, BF_AP, false));    // warm
+    float tbest = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      WD_TRY(b_khat(b, BF_P, BF_AP, false));
+      cudaEventRecord(e1, b->stream);
+      WD_CUDA(cudaEventSynchronize(e1));
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tbest = std::min(tbest, ms);
+    }
+    if (tbest < best) { best = tbest; pick = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  WD_TRY(b_layout(b, pick));
+  b->tuned = true;
+  return WD_OK;
+}
+
+}  // namespace wd
+
+extern "C" {
+
+int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const int* nrhs, wd_batch** out) {
+  if (!ctxs || !kappas || !nrhs || !out || nlat < 1) return fail(WD_ERR_ARG, "wd_batch_create: bad arguments");
+  *out = nullptr;
+  for (int l = 0; l < nlat; ++l) {
+    if (!ctxs[l] || !ctxs[l]->have_gauge) return fail(WD_ERR_STATE, "wd_batch_create: every context needs a gauge field");
+    if (nrhs[l] < 1 || nrhs[l] > B_MAXR) return fail(WD_ERR_ARG, "wd_batch_create: 1 <= nrhs <= 8 per lattice");
+    if (ctxs[l]->stream != ctxs[0]->stream) return fail(WD_ERR_ARG, "wd_batch_create: contexts must share a stream");
+  }
+  wd_batch* b = new (std::nothrow) wd_batch();
+  if (!b) return fail(WD_ERR_ARG, "out of host memory");
+  auto bail = [&](int code) { wd_batch_destroy(b); return code; };
+  b->ctx.assign(ctxs, ctxs + nlat);
+  int s0 = 0;
+  for (int l = 0; l < nlat; ++l) {
+    wd_ctx* c = ctxs[l];
+    BLat L{};
+    L.g = c->g;
+    L.nr = nrhs[l];
+    L.sys0 = s0;
+    L.recon = ctxs[0]->recon == WD_RECON_12 ? 12 : 18;
+    L.kappa = kappas[l];
+    L.g12 = c->gauge32r12;
+    L.g18 = c->gauge32;
+    for (int f = 0; f < BF_N; ++f) {
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, sizeof(float4) * 6 * c->g.Vh * L.nr);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "wd_batch_create: cudaMalloc"));
+      b->mem.push_back(p);
+      L.f[f] = (float4*)p;
+    }
+    s0 += L.nr;
+    b->lat_h.push_back(L);
+  }
+  b->S = s0;
+  cudaError_t e = cudaMalloc(&b->lat_d, sizeof(BLat) * nlat);
+  if (e == cudaSuccess) e = cudaMalloc(&b->st_d, sizeof(CGState) * b->S);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->st_h, sizeof(CGState) * b->S);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "wd_batch_create: allocation"));
+  if (ctxs[0]->stream == nullptr) {   // the legacy stream cannot be captured: use our own
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "wd_batch_create: stream"));
+    b->own_stream = true;
+  } else {
+    b->stream = ctxs[0]->stream;
+  }
+  int s = b_layout(b, 128);
+  if (s != WD_OK) return bail(s);
+  *out = b;
+  return WD_OK;
+}
+
+int wd_batch_destroy(wd_batch* b) {
+  if (!b) return WD_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->mem) cudaFree(p);
+  cudaFree(b->lat_d);
+  cudaFree(b->block_lat_d);
+  cudaFree(b->partial);
+  cudaFree(b->st_d);
+  if (b->st_h) cudaFreeHost(b->st_h);
+  if (b->own_stream) {
+    cudaStreamDestroy(b->stream);
+    cudaEventDestroy(b->ev_in);
+    cudaEventDestroy(b->ev_out);
+  }
+  delete b;
+  return WD_OK;
+}
+
+int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out) {
+  if (!b || !in || !out) return fail(WD_ERR_ARG, "wd_batch_mdagm: null argument");
+  WD_TRY(b_enter(b));
+  for (size_t l = 0; l < b->lat_h.size(); ++l) {
+    const BLat& L = b->lat_h[l];
+    for (int r = 0; r < L.nr; ++r)
+      WD_TRY(b_slot(b, (int)l, r, BF_P, const_cast<double*>(in[l]) + (long)r * 24 * L.g.Vh, 1));
+  }
+  WD_TRY(b_khat(b, BF_P, BF_AP, false));
+  for (size_t l = 0; l < b->lat_h.size(); ++l) {
+    const BLat& L = b->lat_h[l];
+    for (int r = 0; r < L.nr; ++r) WD_TRY(b_slot(b, (int)l, r, BF_AP, out[l] + (long)r * 24 * L.g.Vh, 0));
+  }
+  for (size_t l = 0; l < b->lat_h.size(); ++l) b->ctx[l]->nmat += b->lat_h[l].nr;
+  return b_leave(b);
+}
+
+int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const wd_cg_params* p, int use_graph,
+                wd_cg_info* infos) {
+  if (!b || !bvec || !x || !p) return fail(WD_ERR_ARG, "wd_batch_cg: null argument");
+  if (!(p->tol > 0) || p->maxiter < 1) return fail(WD_ERR_ARG, "wd_batch_cg: tol > 0 and maxiter >= 1");
+  const double delta = (p->delta > 0 && p->delta < 1) ? p->delta : 1e-3;
+  const int check = p->check_every > 0 ? p->check_every : 16;
+  const int nlat = (int)b->lat_h.size();
+  WD_TRY(b_enter(b));
+  // x = 0, r = p = b (interleaved FP32); per-system |b|^2 in FP64
+  std::vector<double> bb(b->S);
+  std::vector<wd_cg_info> info(b->S);
+  std::vector<long long> nmat0(nlat);
+  for (int l = 0; l < nlat; ++l) {
+    const BLat& L = b->lat_h[l];
+    wd_ctx* c = b->ctx[l];
+    nmat0[l] = c->nmat;
+    for (int r = 0; r < L.nr; ++r) {
+      const long off = (long)r * 24 * L.g.Vh;
+      Field bf = wrap_f64(c, bvec[l] + off), xf = wrap_f64(c, x[l] + off);
+      WD_TRY(zero(c, xf));
+      WD_TRY(norm2(c, bf, &bb[L.sys0 + r]));
+      WD_TRY(b_slot(b, l, r, BF_R, const_cast<double*>(bvec[l]) + off, 1));
+      WD_TRY(b_slot(b, l, r, BF_P, const_cast<double*>(bvec[l]) + off, 1));
+      WD_TRY(b_slot(b, l, r, BF_X, nullptr, 2));
+    }
+  }
+  for (int s = 0; s < b->S; ++s) {
+    CGState& S = b->st_h[s];
+    S = CGState{};
+    S.rr = S.rr_old = bb[s];
+    S.stop_rr = p->tol * p->tol * bb[s];
+    S.upd_rr = std::max(delta * delta * bb[s], S.stop_rr);
+    S.maxiter = p->maxiter;
+    S.flag = (bb[s] == 0.0) ? FLAG_DONE : 0;
+  }
+  WD_CUDA(cudaMemcpyAsync(b->st_d, b->st_h, sizeof(CGState) * b->S, cudaMemcpyHostToDevice, b->stream));
+  if (!b->tuned) {
+    // tune on K_hat p (p = b: real data); the pAp it leaves is recomputed
+    WD_TRY(b_autotune(b));
+  }
+  // a chunk of iterations, optionally as one CUDA graph
+  if (use_graph && (b->graph == nullptr || b->graph_iters != check)) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaGraph_t g;
+    WD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = b->launches;
+    int s = WD_OK;
+    for (int k = 0; k < check && s == WD_OK; ++k) s = b_iteration(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    b->launches = l0;
+    if (s != WD_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "wd_batch_cg: graph capture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "wd_batch_cg: graph instantiate");
+    b->graph_iters = check;
+  }
+  const int per_iter = 8;
+  int status = WD_OK;
+  for (;;) {
+    if (use_graph) {
+      WD_CUDA(cudaGraphLaunch(b->graph, b->stream));
+      b->launches += (long long)per_iter * check;
+    } else {
+      for (int k = 0; k < check; ++k) WD_TRY(b_iteration(b));
+    }
+    for (int l = 0; l < nlat; ++l) b->ctx[l]->nmat += (long long)check * b->lat_h[l].nr;
+    WD_CUDA(cudaMemcpyAsync(b->st_h, b->st_d, sizeof(CGState) * b->S, cudaMemcpyDeviceToHost, b->stream));
+    WD_CUDA(cudaStreamSynchronize(b->stream));
+    bool all_done = true, changed = false;
+    for (int l = 0; l < nlat && status == WD_OK; ++l) {
+      const BLat& L = b->lat_h[l];
+      wd_ctx* c = b->ctx[l];
+      for (int r = 0; r < L.nr; ++r) {
+        const int sidx = L.sys0 + r;
+        CGState& S = b->st_h[sidx];
+        if (S.flag == FLAG_DONE) continue;
+        if (S.flag & FLAG_NAN) { status = fail(WD_ERR_NAN, "wd_batch_cg: non-finite value"); break; }
+        if (S.flag == 0) { all_done = false; continue; }
+        // reliable update of this system in FP64 on its own lattice
+        const long off = (long)r * 24 * L.g.Vh;
+        Field xf = wrap_f64(c, x[l] + off), bf = wrap_f64(c, bvec[l] + off);
+        WsGuard w(c);
+        Field t, rr, t1, t2;
+        WD_TRY(w.get(WD_F64, &t));
+        WD_TRY(w.get(WD_F64, &rr));
+        WD_TRY(w.get(WD_F64, &t1));
+        WD_TRY(w.get(WD_F64, &t2));
+        WD_TRY(b_slot(b, l, r, BF_X, (double*)t.data, 0));
+        WD_TRY(b_slot(b, l, r, BF_X, nullptr, 2));
+        if (b->own_stream) {   // the context stream works on what the batch stream produced
+          WD_CUDA(cudaEventRecord(b->ev_out, b->stream));
+          WD_CUDA(cudaStreamWaitEvent(c->stream, b->ev_out, 0));
+        }
+        WD_TRY(axpby(c, 1.0, xf, 1.0, t, xf));
+        WD_TRY(apply_khat(c, L.kappa, xf, t, t1, t2, false, false));
+        WD_TRY(axpby(c, 1.0, bf, -1.0, t, rr));
+        double rr2;
+        WD_TRY(norm2(c, rr, &rr2));
+        info[sidx].reliable_updates += 1;
+        info[sidx].iters = S.iter;
+        info[sidx].true_rel_resid = std::sqrt(rr2 / bb[sidx]);
+        changed = true;
+        if (!std::isfinite(rr2)) { status = fail(WD_ERR_NAN, "wd_batch_cg: non-finite residual"); break; }
+        if (rr2 <= S.stop_rr) { S.flag = FLAG_DONE; continue; }
+        if (S.flag & FLAG_MAXITER) { status = fail(WD_ERR_NOCONV, "wd_batch_cg: maxiter reached"); break; }
+        all_done = false;
+        WD_TRY(b_slot(b, l, r, BF_R, (double*)rr.data, 1));
+        const double beta = rr2 / S.rr_old;
+        k_slot_pupdate<<<nblocks(L.g.Vh, 128), 128, 0, b->stream>>>(L.g.Vh, L.nr, r, L.f[BF_P], L.f[BF_R],
+                                                                    (float)beta);
+        b->launches += 1;
+        S.rr = rr2;
+        S.upd_rr = std::max(delta * delta * rr2, S.stop_rr);
+        S.flag = 0;
+      }
+    }
+    if (status != WD_OK) break;
+    if (changed) WD_CUDA(cudaMemcpyAsync(b->st_d, b->st_h, sizeof(CGState) * b->S, cudaMemcpyHostToDevice, b->stream));
+    if (all_done) break;
+  }
+  for (int l = 0; l < nlat && infos; ++l) {
+    const BLat& L = b->lat_h[l];
+    for (int r = 0; r < L.nr; ++r) {
+      const int sidx = L.sys0 + r;
+      info[sidx].n_mat = info[sidx].iters + info[sidx].reliable_updates;
+      infos[sidx] = info[sidx];
+    }
+  }
+  WD_TRY(b_leave(b));
+  return status;
+}
+
+int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches) {
+  if (!b) return fail(WD_ERR_ARG, "null batch");
+  if (n_systems) *n_systems = b->S;
+  if (threads) *threads = b->threads;
+  if (launches) *launches = b->launches;
+  return WD_OK;
+}
+
+}  // extern "C"

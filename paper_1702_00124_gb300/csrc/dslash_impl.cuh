@@ -155,16 +155,17 @@ __global__ void __launch_bounds__(HOP_MAXT, MINB) k_hop(HopArgs<In, Out, Y, G> a
   }
 }
 
-// Launch-shape autotuner.  Candidates: block sizes 64/128/256 with the
-// compiler's register choice, and 128/256 with registers capped at 64 for
-// occupancy.  The first launch of a (formats, links, dagger, epilogue,
-// volume) key outside a queued CG chunk times every candidate with CUDA events
-// on the context stream (all candidates compute the same output) and keeps
-// the fastest; the NORM variant reuses the shape of its key.
+// Launch-shape autotuner.  Candidates: block sizes 128/256/64 with the
+// compiler's register choice.  (Capping registers at 64 for occupancy spills
+// in every FP32 variant; it won in isolated timings but lost 4-5 % inside the
+// trajectory, so it is not a candidate; k_hop keeps the MINB parameter.)
+// The first launches of a (formats, links, dagger, epilogue, volume) key
+// outside a queued CG chunk cycle through the candidates (see hop_dispatch);
+// the NORM variant reuses the shape of its key.
 struct HopCfg {
   int threads, minb;
 };
-constexpr HopCfg HOP_CANDIDATES[] = {{128, 1}, {256, 1}, {64, 1}, {128, 4}, {256, 4}};
+constexpr HopCfg HOP_CANDIDATES[] = {{128, 1}, {256, 1}, {64, 1}};
 constexpr int HOP_NCAND = sizeof(HOP_CANDIDATES) / sizeof(HOP_CANDIDATES[0]);
 
 template <class T, bool D, bool X, bool N, class In, class Out, class Y, class G>

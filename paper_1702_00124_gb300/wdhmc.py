@@ -108,6 +108,11 @@ _SIG = {
     "wd_set_residual": ([_P, _I], _I),
     "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
     "wd_tune_entry": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I)], _I),
+    "wd_batch_create": ([C.POINTER(_P), _I, C.POINTER(_D), C.POINTER(_I), C.POINTER(_P)], _I),
+    "wd_batch_destroy": ([_P], _I),
+    "wd_batch_mdagm": ([_P, C.POINTER(_P), C.POINTER(_P)], _I),
+    "wd_batch_cg": ([_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(wd_cg_params), _I, C.POINTER(wd_cg_info)], _I),
+    "wd_batch_info": ([_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -175,6 +180,49 @@ def metropolis(dH, u):
     a = C.c_int(0)
     _check(lib.metropolis(dH, u, C.byref(a)))
     return bool(a.value)
+
+
+class Batch:
+    """wd_batch: independent lattices (Lattice objects sharing a stream), each
+    with a hopping parameter and 1..8 right-hand sides."""
+
+    def __init__(self, lattices, kappas, nrhs):
+        n = len(lattices)
+        self.lattices, self.nrhs = list(lattices), list(nrhs)
+        hs = (_P * n)(*[lat.h.value for lat in lattices])
+        h = C.c_void_p()
+        _check(lib.wd_batch_create(hs, n, (_D * n)(*kappas), (_I * n)(*nrhs), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.wd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptrs(ts):
+        return (_P * len(ts))(*[_ptr(t).value for t in ts])
+
+    def wd_batch_mdagm(self, ins, outs):
+        _check(lib.wd_batch_mdagm(self.h, self._ptrs(ins), self._ptrs(outs)))
+
+    def wd_batch_cg(self, bs, xs, params, use_graph=True):
+        S = sum(self.nrhs)
+        infos = (wd_cg_info * S)()
+        _check(lib.wd_batch_cg(self.h, self._ptrs(bs), self._ptrs(xs), C.byref(params), int(use_graph), infos))
+        return [dict(iters=i.iters, reliable_updates=i.reliable_updates, n_mat=i.n_mat,
+                     true_rel_resid=i.true_rel_resid) for i in infos]
+
+    def wd_batch_info(self):
+        s, t, n = C.c_int(0), C.c_int(0), C.c_longlong(0)
+        _check(lib.wd_batch_info(self.h, C.byref(s), C.byref(t), C.byref(n)))
+        return dict(systems=s.value, threads=t.value, launches=n.value)
 
 
 class Lattice:
