@@ -59,6 +59,7 @@ struct BArgs {
   CGState* st;             // per system
   double* partial;         // [block][B_MAXR]
   int out_par;
+  int use_flags;           // inside CG: systems with a stop flag do no work
 };
 
 __device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& cb, int& r, int& s) {
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& c
   cb = item / L->nr;
   r = (int)(item - cb * L->nr);
   s = L->sys0 + r;
-  return a.st[s].flag == 0;
+  return !a.use_flags || a.st[s].flag == 0;
 }
 
 __device__ __forceinline__ void b_block_partial(const BArgs& a, double (&v)[B_MAXR]) {
@@ -263,6 +264,7 @@ struct wd_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   long long launches = 0;
+  int in_cg = 0;                 // launches belong to a CG iteration
   std::vector<void*> mem;
 };
 
@@ -295,7 +297,7 @@ static int b_layout(wd_batch* b, int threads) {
 }
 
 static BArgs b_args(wd_batch* b, int out_par) {
-  return BArgs{b->lat_d, b->block_lat_d, b->st_d, b->partial, out_par};
+  return BArgs{b->lat_d, b->block_lat_d, b->st_d, b->partial, out_par, b->in_cg};
 }
 
 static int b_hop(wd_batch* b, int out_par, bool dag, int fin, int fout, int fy, bool norm) {
@@ -342,11 +344,16 @@ static int b_khat(wd_batch* b, int fin, int fout, bool norm) {
 }
 
 static int b_iteration(wd_batch* b) {
-  WD_TRY(b_khat(b, BF_P, BF_AP, true));
-  k_bupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
-  k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 1);
-  k_bpupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
-  b->launches += 3;
+  b->in_cg = 1;   // systems that carry a stop flag skip their work
+  int s = b_khat(b, BF_P, BF_AP, true);
+  if (s == WD_OK) {
+    k_bupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
+    k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 1);
+    k_bpupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
+    b->launches += 3;
+  }
+  b->in_cg = 0;
+  WD_TRY(s);
   WD_CUDA(cudaGetLastError());
   return WD_OK;
 }
@@ -443,6 +450,7 @@ int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const i
   cudaError_t e = cudaMalloc(&b->lat_d, sizeof(BLat) * nlat);
   if (e == cudaSuccess) e = cudaMalloc(&b->st_d, sizeof(CGState) * b->S);
   if (e == cudaSuccess) e = cudaMallocHost(&b->st_h, sizeof(CGState) * b->S);
+  if (e == cudaSuccess) e = cudaMemset(b->st_d, 0, sizeof(CGState) * b->S);
   if (e != cudaSuccess) return bail(cuda_fail(e, "wd_batch_create: allocation"));
   if (ctxs[0]->stream == nullptr) {   // the legacy stream cannot be captured: use our own
     e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
