@@ -380,31 +380,40 @@ static int b_leave(wd_batch* b) {
 }
 
 // Time the batched K_hat for each candidate block size; keep the fastest.
+// Rounds with the candidate order rotated; median per candidate; the default
+// 128 is replaced only by a candidate at least 3 % faster.
 static int b_autotune(wd_batch* b) {
-  const int cand[] = {128, 256, 64};
-  float best = 1e30f;
-  int pick = 128;
+  constexpr int NC = 3, ROUNDS = 5;
+  const int cand[NC] = {128, 256, 64};
+  std::vector<float> t[NC];
   cudaEvent_t e0, e1;
   WD_CUDA(cudaEventCreate(&e0));
   WD_CUDA(cudaEventCreate(&e1));
-  for (int t : cand) {
-    WD_TRY(b_layout(b, t));
-    WD_TRY(b_khat(b, BF_P, BF_AP, false));    // warm
-    float tbest = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+  WD_TRY(b_khat(b, BF_P, BF_AP, false));      // warm
+  for (int r = 0; r < ROUNDS; ++r) {
+    for (int j = 0; j < NC; ++j) {
+      const int k = (j + r) % NC;
+      WD_TRY(b_layout(b, cand[k]));
       cudaEventRecord(e0, b->stream);
       WD_TRY(b_khat(b, BF_P, BF_AP, false));
       cudaEventRecord(e1, b->stream);
       WD_CUDA(cudaEventSynchronize(e1));
       float ms;
       cudaEventElapsedTime(&ms, e0, e1);
-      tbest = std::min(tbest, ms);
+      t[k].push_back(ms);
     }
-    if (tbest < best) { best = tbest; pick = t; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  WD_TRY(b_layout(b, pick));
+  float med[NC];
+  for (int k = 0; k < NC; ++k) {
+    std::sort(t[k].begin(), t[k].end());
+    med[k] = t[k][t[k].size() / 2];
+  }
+  int pick = 0;
+  for (int k = 1; k < NC; ++k)
+    if (med[k] < 0.97f * med[pick]) pick = k;
+  WD_TRY(b_layout(b, cand[pick]));
   b->tuned = true;
   return WD_OK;
 }

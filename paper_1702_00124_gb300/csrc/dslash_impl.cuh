@@ -7,6 +7,8 @@
 // is rebuilt from the upper half.  Optional epilogue: out = y + alpha * D psi,
 // with the FP64 grid sum of |out|^2 (pAp = |M_hat p|^2 for CG).
 #pragma once
+#include <algorithm>
+
 #include "wd_internal.cuh"
 
 namespace wd {
@@ -180,22 +182,34 @@ void hop_launch_cfg(wd_ctx* c, HopCfg cfg, const HopArgs<In, Out, Y, G>& a) {
 // bracketed by CUDA events (so every candidate is timed in the data flow it
 // serves: inputs just written by the producing kernel, L2 as in production).
 // When all samples are in, the best time per candidate decides.
-constexpr int TUNE_ROUNDS = 3;
+// The candidate order rotates from round to round (a clock ramp or a cache
+// state favours no candidate), a candidate's score is its median time, and the
+// default shape is replaced only by a candidate at least 3 % faster.
+constexpr int TUNE_ROUNDS = 5;
+
+inline int tune_candidate(int sample) {
+  const int round = sample / HOP_NCAND;
+  return (sample + round) % HOP_NCAND;
+}
 
 inline int tune_settle(wd_ctx* c, long long key, TuneSamples& s) {
   WD_CUDA(cudaEventSynchronize(s.ev.back()));
-  float best = 1e30f;
-  int pick = 0;
+  float med[HOP_NCAND];
   for (int k = 0; k < HOP_NCAND; ++k) {
-    float kbest = 1e30f;
-    for (int r = 0; r < TUNE_ROUNDS; ++r) {
-      const int i = r * HOP_NCAND + k;
+    float t[TUNE_ROUNDS];
+    int n = 0;
+    for (int i = 0; i < HOP_NCAND * TUNE_ROUNDS; ++i) {
+      if (tune_candidate(i) != k) continue;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]);
-      kbest = ms < kbest ? ms : kbest;
+      t[n++] = ms;
     }
-    if (kbest < best) { best = kbest; pick = k; }
+    std::sort(t, t + n);
+    med[k] = t[n / 2];
   }
+  int pick = 0;
+  for (int k = 1; k < HOP_NCAND; ++k)
+    if (med[k] < 0.97f * med[pick]) pick = k;
   for (auto& e : s.ev) cudaEventDestroy(e);
   c->tune_samples.erase(key);
   c->tune[key] = {HOP_CANDIDATES[pick].threads, HOP_CANDIDATES[pick].minb};
@@ -210,8 +224,8 @@ int hop_dispatch(wd_ctx* c, long long key, bool may_tune, const HopArgs<In, Out,
     cfg = HopCfg{it->second.first, it->second.second};
   } else if (may_tune && c->autotune && !N) {
     TuneSamples& s = c->tune_samples[key];
-    const int i = (int)s.ev.size() / 2;               // sample index: round * NCAND + candidate
-    cfg = HOP_CANDIDATES[i % HOP_NCAND];
+    const int i = (int)s.ev.size() / 2;               // sample index
+    cfg = HOP_CANDIDATES[tune_candidate(i)];
     cudaEvent_t e0, e1;
     WD_CUDA(cudaEventCreate(&e0));
     WD_CUDA(cudaEventCreate(&e1));
