@@ -137,8 +137,8 @@ int wd_set_autotune(wd_ctx* ctx, int enable, int* n_tuned);
 /* The index-th tuned entry: its key (((in*8 + out)*8 + y)*4 + links)*4 +
  * 2 dagger + xpay, with formats as enum wd_prec (y = 7 without epilogue) and
  * links 0 FP64, 1 FP32 18 reals, 2 FP32 12 reals, 3 double-float), the chosen
- * block size and minimum blocks per SM (4 = registers capped at 64). */
-int wd_tune_entry(wd_ctx* ctx, int index, long long* key, int* threads, int* minb);
+ * block size and the launch bound (128 or 256) the chosen kernel is compiled for. */
+int wd_tune_entry(wd_ctx* ctx, int index, long long* key, int* threads, int* maxt);
 /* Volume helpers: out[0] = V, out[1] = Vh. */
 int wd_volume(const wd_ctx* ctx, long long out[2]);
 

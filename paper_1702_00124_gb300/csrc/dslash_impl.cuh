@@ -112,9 +112,9 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int par, long cb, const i
   }
 }
 
-// MINB > 1 caps the registers (65536 / (256 MINB) per thread) for occupancy.
-template <class T, bool DAG, bool XPAY, bool NORM, int MINB, class In, class Out, class Y, class G>
-__global__ void __launch_bounds__(HOP_MAXT, MINB) k_hop(HopArgs<In, Out, Y, G> a) {
+// MAXT: the largest block size the compiled kernel may be launched with.
+template <class T, bool DAG, bool XPAY, bool NORM, int MAXT, class In, class Out, class Y, class G>
+__global__ void __launch_bounds__(MAXT) k_hop(HopArgs<In, Out, Y, G> a) {
   if (a.st != nullptr && a.st->flag != 0) return;
   const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
@@ -157,24 +157,25 @@ __global__ void __launch_bounds__(HOP_MAXT, MINB) k_hop(HopArgs<In, Out, Y, G> a
   }
 }
 
-// Launch-shape autotuner.  Candidates: block sizes 128/256/64 with the
-// compiler's register choice.  (Capping registers at 64 for occupancy spills
-// in every FP32 variant; it won in isolated timings but lost 4-5 % inside the
-// trajectory, so it is not a candidate; k_hop keeps the MINB parameter.)
-// The first launches of a (formats, links, dagger, epilogue, volume) key
-// outside a queued CG chunk cycle through the candidates (see hop_dispatch);
-// the NORM variant reuses the shape of its key.
+// Launch-shape autotuner.  Candidates: block sizes 128 and 64 with the kernel
+// compiled for at most 128 threads (FP32: 86-88 registers, no spills), and
+// 256 with a kernel compiled for 256 threads (the compiler then takes up to
+// 255 registers).  Register caps below the compiler's choice spill and lost
+// 4-5 % inside the trajectory, so none is a candidate.  The first launches of
+// a (formats, links, dagger, epilogue, volume) key outside a queued CG chunk
+// cycle through the candidates (see hop_dispatch); the NORM variant reuses
+// the shape of its key.
 struct HopCfg {
-  int threads, minb;
+  int threads, maxt;   // block size; the launch bound the kernel is compiled for
 };
-constexpr HopCfg HOP_CANDIDATES[] = {{128, 1}, {256, 1}, {64, 1}};
+constexpr HopCfg HOP_CANDIDATES[] = {{128, 128}, {256, 256}, {64, 128}};
 constexpr int HOP_NCAND = sizeof(HOP_CANDIDATES) / sizeof(HOP_CANDIDATES[0]);
 
 template <class T, bool D, bool X, bool N, class In, class Out, class Y, class G>
 void hop_launch_cfg(wd_ctx* c, HopCfg cfg, const HopArgs<In, Out, Y, G>& a) {
   const int nb = nblocks(c->g.Vh, cfg.threads);
-  if (cfg.minb == 4) k_hop<T, D, X, N, 4, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
-  else k_hop<T, D, X, N, 1, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
+  if (cfg.maxt == 256) k_hop<T, D, X, N, 256, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
+  else k_hop<T, D, X, N, 128, In, Out, Y, G><<<nb, cfg.threads, 0, c->stream>>>(a);
 }
 
 // Online tuning: the first HOP_NCAND * TUNE_ROUNDS tunable launches of a key
@@ -212,7 +213,7 @@ inline int tune_settle(wd_ctx* c, long long key, TuneSamples& s) {
     if (med[k] < 0.97f * med[pick]) pick = k;
   for (auto& e : s.ev) cudaEventDestroy(e);
   c->tune_samples.erase(key);
-  c->tune[key] = {HOP_CANDIDATES[pick].threads, HOP_CANDIDATES[pick].minb};
+  c->tune[key] = {HOP_CANDIDATES[pick].threads, HOP_CANDIDATES[pick].maxt};
   return WD_OK;
 }
 

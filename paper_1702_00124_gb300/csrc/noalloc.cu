@@ -58,7 +58,7 @@ int launch(cudaStream_t s, const Geom& g, int out_par, const double2* gauge, con
   using A = HopArgs<SpF64, SpF64, SpF64, GF64>;
   SpF64 I{const_cast<double2*>(in), g.Vh}, O{out, g.Vh}, Y{const_cast<double2*>(y ? y : in), g.Vh};
   A a{g, out_par, I, O, Y, GF64{gauge, g.Vh}, alpha, Reduce{nullptr, nullptr, nullptr}, nullptr};
-  k_hop<double, DAG, XPAY, false, 1, SpF64, SpF64, SpF64, GF64><<<nblocks(g.Vh, HOP_THREADS), HOP_THREADS, 0, s>>>(a);
+  k_hop<double, DAG, XPAY, false, 128, SpF64, SpF64, SpF64, GF64><<<nblocks(g.Vh, HOP_THREADS), HOP_THREADS, 0, s>>>(a);
   WD_CUDA(cudaGetLastError());
   return WD_OK;
 }
