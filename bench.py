@@ -308,7 +308,16 @@ def main():
     launches = lat.wd_launch_count() - l0
     nmat = (lat.wd_nmat() - n0) / args.steps
     prof = lat.wd_profile_read(wd.F32)
+    prof64 = lat.wd_profile_read(wd.F64)
+    counts = lat.wd_hop_counts()
     lat.wd_profile_enable(0)
+    # share of the timed region spent in each hop family: all launches of the
+    # family x its average sampled duration
+    shares = {}
+    for name, pr, n in (("k_hop_fp32", prof, counts[wd.F32]), ("k_hop_fp64", prof64, counts[wd.F64])):
+        if pr["launches"]:
+            shares[name] = {"launches": n, "avg_ms": pr["ms"] / pr["launches"],
+                            "share": n * pr["ms"] / pr["launches"] / (elapsed * 1e3)}
     clk = clocks.stop()
     t_max = elapsed
     if dist:
@@ -420,6 +429,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "working set (1.2 GB FP64 links + FP32 copies) far above the 126 MB L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "hop_time_shares": shares,
                 "clocks": clk,
                 "trajectory": {"dH": [float(r["dH"]) for r in timed], "accepted": acc,
                                "n_mat_per_traj": nmat, "force_evals": [r["n_force_evals"] for r in timed],

@@ -337,6 +337,9 @@ int wd_profile_enable(wd_ctx* ctx, int every_n);
 int wd_profile_read(wd_ctx* ctx, int fmt, long long* launches, double* total_ms, double* bytes);
 /* Kernels launched by this context since it was created. */
 int wd_launch_count(wd_ctx* ctx, long long* count);
+/* Hop launches per input format (FP64, FP32, FP16, BF16, double-float) since
+ * the last wd_profile_enable, sampled or not. */
+int wd_hop_counts(wd_ctx* ctx, long long counts[5]);
 
 #ifdef __cplusplus
 }

@@ -319,7 +319,7 @@ int wd_profile_enable(wd_ctx* c, int every_n) {
   Prof& p = c->prof;
   p.every = every_n;
   p.seen = 0;
-  for (int f = 0; f < Prof::NF; ++f) { p.launches[f] = 0; p.ms[f] = 0.0; p.bytes[f] = 0.0; }
+  for (int f = 0; f < Prof::NF; ++f) { p.launches[f] = 0; p.ms[f] = 0.0; p.bytes[f] = 0.0; p.all[f] = 0; }
   for (auto& e : p.ev) cudaEventDestroy(e);
   p.ev.clear();
   p.ev_bytes.clear();
@@ -356,6 +356,13 @@ int wd_profile_read(wd_ctx* c, int fmt, long long* launches, double* total_ms, d
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
   if (bytes) *bytes = b;
+  return WD_OK;
+}
+
+int wd_hop_counts(wd_ctx* c, long long counts[5]) {
+  CHECK_CTX(c);
+  CHECK_PTR(counts);
+  for (int f = 0; f < Prof::NF; ++f) counts[f] = c->prof.all[f];
   return WD_OK;
 }
 

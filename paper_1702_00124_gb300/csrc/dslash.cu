@@ -57,6 +57,7 @@ int hop(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out, con
   // Launches queued inside a CG chunk may return at once after convergence;
   // only launches that always do their work are sampled.
   cudaEvent_t e0 = nullptr;
+  if (in.fmt >= 0 && in.fmt < Prof::NF) c->prof.all[in.fmt] += 1;
   if (!in_cg) prof_begin(c, &e0);
   int s;
   if (in.fmt == WD_F64) s = hop_f64(c, out_par, dag, in, out, y, alpha, norm_cg, in_cg);

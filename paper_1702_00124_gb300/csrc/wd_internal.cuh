@@ -414,6 +414,7 @@ struct Prof {
   int every = 0;
   long long seen = 0;
   static constexpr int NF = 5;      // FP64, FP32, FP16, BF16, double-float
+  long long all[NF] = {0, 0, 0, 0, 0};          // every hop launch, sampled or not
   long long launches[NF] = {0, 0, 0, 0, 0};
   double ms[NF] = {0, 0, 0, 0, 0};
   double bytes[NF] = {0, 0, 0, 0, 0};

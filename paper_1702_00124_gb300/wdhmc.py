@@ -108,6 +108,7 @@ _SIG = {
     "wd_set_residual": ([_P, _I], _I),
     "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
     "wd_tune_entry": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I)], _I),
+    "wd_hop_counts": ([_P, C.POINTER(C.c_longlong)], _I),
     "wd_batch_create": ([C.POINTER(_P), _I, C.POINTER(_D), C.POINTER(_I), C.POINTER(_P)], _I),
     "wd_batch_destroy": ([_P], _I),
     "wd_batch_mdagm": ([_P, C.POINTER(_P), C.POINTER(_P)], _I),
@@ -383,6 +384,11 @@ class Lattice:
         n, ms, b = C.c_longlong(0), C.c_double(0), C.c_double(0)
         _check(lib.wd_profile_read(self.h, fmt, C.byref(n), C.byref(ms), C.byref(b)))
         return dict(launches=n.value, ms=ms.value, bytes=b.value)
+
+    def wd_hop_counts(self):
+        a = (C.c_longlong * 5)()
+        _check(lib.wd_hop_counts(self.h, a))
+        return list(a)
 
     def wd_launch_count(self):
         n = C.c_longlong(0)
