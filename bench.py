@@ -218,7 +218,7 @@ def kernel_case(args):
     lat.wd_gauge_load(U_dev)
     del U_dev
     prec, recon = {"khat_f32_recon12": (wd.F32, 1), "khat_bf16_recon12": (wd.BF16, 1),
-                   "khat_f64": (wd.F64, 0)}[args.kernel_case]
+                   "khat_f64": (wd.F64, 0), "khat_df": (wd.DF, 0)}[args.kernel_case]
     lat.wd_set_recon(recon)
     x, y = lat.half_spinor(), lat.half_spinor()
     lat.gaussian_draw(0, 0, 1, 1, x)
@@ -237,7 +237,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-vs-FP64 and e2e measurements")
-    ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64"],
+    ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64", "khat_df"],
                     help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
     ap.add_argument("--reps", type=int, default=4)
     args = ap.parse_args()
