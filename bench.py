@@ -46,9 +46,9 @@ DEFAULT_WORKLOAD = "c5_32x32x32x64"
 # group 0: filtered + Hasenbusch terms, group 1: P(J) term, -1: gauge action.
 LEVELS = [(0, 10), (1, 1), (-1, 2)]
 # Residual recomputation of the mixed-precision solves: 0 = FP64, 1 =
-# double-float (2 x FP32).  The double-float hop measured 2.44 ms against
-# 2.08 ms for FP64 at this volume (latency-bound at 164 registers), so FP64.
-RESIDUAL_MODE = 0
+# double-float (2 x FP32, about 44-48 bits; b, x, r and dots stay FP64).
+# At this volume the double-float hop takes 0.70 ms against 2.08 ms in FP64.
+RESIDUAL_MODE = 1
 # K_hat applications of one trajectory of the default workload, counted by
 # the library's N_mat counter (algorithmic count; the reference arm scales
 # its per-K_hat time by it).

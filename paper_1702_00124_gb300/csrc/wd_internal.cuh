@@ -73,12 +73,11 @@ __host__ __device__ __forceinline__ dd dd_2sum(float a, float b) {
   const float bb = s - a;
   return dd(s, (a - (s - bb)) + (b - bb));
 }
+// Sum with an exact two-sum of the high words and the low words added in
+// FP32 (Dekker): relative error about 2^-44 unless the operands cancel.
 __host__ __device__ __forceinline__ dd operator+(dd a, dd b) {
   dd s = dd_2sum(a.hi, b.hi);
-  const dd t = dd_2sum(a.lo, b.lo);
-  s.lo += t.hi;
-  s = dd_fast2sum(s.hi, s.lo);
-  s.lo += t.lo;
+  s.lo += a.lo + b.lo;
   return dd_fast2sum(s.hi, s.lo);
 }
 __host__ __device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
