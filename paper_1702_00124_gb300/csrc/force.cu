@@ -151,6 +151,97 @@ int force_outer(wd_ctx* c, double coef, const Field& Ye, const Field& Yo, const 
   return WD_OK;
 }
 
+// Two (Y, X) pairs in one pass: F += coef0 * dRe(Y0^dag D X0) + coef1 * dRe(Y1^dag D X1),
+// so the links and F are read and written once for both (the polynomial-term force
+// has two pairs per factor).
+template <class S, class G>
+struct ForceArgs2 {
+  Geom g;
+  S Ye[2], Yo[2], Xe[2], Xo[2];
+  G gauge;
+  double coef[2];
+  double* F;
+};
+
+template <int MU, class T, class S, class G>
+__device__ __forceinline__ void force_dir2(const ForceArgs2<S, G>& a, int par, long cb, const int (&c)[4]) {
+  const Geom& g = a.g;
+  int n[4] = {c[0], c[1], c[2], c[3]};
+  n[MU] = (n[MU] + 1 == g.L[MU]) ? 0 : n[MU] + 1;
+  const long nb = g.cb_of(n[0], n[1], n[2], n[3]);
+  cpx<T> U[9];
+  a.gauge.load(MU, par, cb, U);
+  const T bc = (MU == 3 && c[3] == g.L[3] - 1) ? (T)-1 : (T)1;
+  double fs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    cpx<T> Xs[12], Ys[12], Xn[12], Yn[12];
+    (par ? a.Xo[p] : a.Xe[p]).loadT(cb, Xs);
+    (par ? a.Yo[p] : a.Ye[p]).loadT(cb, Ys);
+    (par ? a.Xe[p] : a.Xo[p]).loadT(nb, Xn);
+    (par ? a.Ye[p] : a.Yo[p]).loadT(nb, Yn);
+    cpx<T> A1[9], A2[9], h[6], k[6];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) { A1[j] = mk<T>(0, 0); A2[j] = mk<T>(0, 0); }
+    half_of<MU, -1>(Xn, h);
+    half_of<MU, -1>(Ys, k);
+    outer_acc(A1, h, k);
+    half_of<MU, +1>(Xs, h);
+    half_of<MU, +1>(Yn, k);
+    outer_acc(A2, h, k);
+    cpx<T> W[9], t[9];
+    mat_mul(U, A1, W);
+    mat_mul_nd(A2, U, t);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) W[j] = bc * (W[j] - t[j]);
+    T f[8];
+    proj_ta(W, f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) fs[q] += a.coef[p] * (double)f[q];
+  }
+  double* F = a.F + ((long)(MU * 2 + par) * 8) * g.Vh + cb;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) F[q * g.Vh] += fs[q];
+}
+
+template <class T, class S, class G>
+__global__ void __launch_bounds__(F_THREADS) k_force2(ForceArgs2<S, G> a) {
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 2 * a.g.Vh) return;
+  const int par = (int)(tid / a.g.Vh);
+  const long cb = tid - par * a.g.Vh;
+  int c[4];
+  a.g.coords(cb, par, c);
+  force_dir2<0, T>(a, par, cb, c);
+  force_dir2<1, T>(a, par, cb, c);
+  force_dir2<2, T>(a, par, cb, c);
+  force_dir2<3, T>(a, par, cb, c);
+}
+
+int force_outer2(wd_ctx* c, const double coef[2], const Field* Ye, const Field* Yo, const Field* Xe,
+                 const Field* Xo, double* F) {
+  const int nb = nblocks(2 * c->g.Vh, F_THREADS);
+  const int f = Ye[0].fmt;
+  for (int p = 0; p < 2; ++p)
+    if (Ye[p].fmt != f || Yo[p].fmt != f || Xe[p].fmt != f || Xo[p].fmt != f)
+      return fail(WD_ERR_ARG, "force2: formats differ");
+  if (f == WD_F64) {
+    ForceArgs2<SpF64, GF64> a{c->g, {sp64(Ye[0]), sp64(Ye[1])}, {sp64(Yo[0]), sp64(Yo[1])},
+                              {sp64(Xe[0]), sp64(Xe[1])}, {sp64(Xo[0]), sp64(Xo[1])},
+                              GF64{c->gauge64, c->g.Vh}, {coef[0], coef[1]}, F};
+    k_force2<double><<<nb, F_THREADS, 0, c->stream>>>(a);
+  } else if (f == WD_F32) {
+    ForceArgs2<SpF32, GF32> a{c->g, {sp32(Ye[0]), sp32(Ye[1])}, {sp32(Yo[0]), sp32(Yo[1])},
+                              {sp32(Xe[0]), sp32(Xe[1])}, {sp32(Xo[0]), sp32(Xo[1])},
+                              GF32{c->gauge32, c->g.Vh}, {coef[0], coef[1]}, F};
+    k_force2<float><<<nb, F_THREADS, 0, c->stream>>>(a);
+  } else {
+    return fail(WD_ERR_ARG, "force2: fields must be FP64 or FP32");
+  }
+  WD_CHECK_LAUNCH();
+  return WD_OK;
+}
+
 // ----------------------------------------------------------------------------
 // gauge action and force
 template <class T, class G>

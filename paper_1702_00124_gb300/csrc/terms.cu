@@ -86,14 +86,11 @@ static int poly_force(wd_ctx* c, double kappa, const std::vector<double>& rr, co
   const int nseg = (m + seg - 1) / seg;
   WsGuard w(c);
   std::vector<Field> cp(nseg), buf(seg);
-  Field L, Ln, ML, MR, cur;
+  Field L, Ln, ML, MR, cur, Lo, Ro, MLo, MRo;
   for (auto& x : cp) WD_TRY(w.get(f, &x));
   for (auto& x : buf) WD_TRY(w.get(f, &x));
-  WD_TRY(w.get(f, &L));
-  WD_TRY(w.get(f, &Ln));
-  WD_TRY(w.get(f, &ML));
-  WD_TRY(w.get(f, &MR));
-  WD_TRY(w.get(f, &cur));
+  for (Field* x : {&L, &Ln, &ML, &MR, &cur, &Lo, &Ro, &MLo, &MRo}) WD_TRY(w.get(f, x));
+  const double k2 = kappa * kappa;
   auto seg_end = [&](int s) { return std::min((s + 1) * seg, m) - 1; };
   // backward pass: R_{m-1} = v, R_{k-1} = (K - r_k) R_k; keep R at segment ends
   WD_TRY(convert(c, v, cur));
@@ -109,12 +106,23 @@ static int poly_force(wd_ctx* c, double kappa, const std::vector<double>& rr, co
     for (int j = b - a; j >= 1; --j) WD_TRY(k_minus(c, kappa, rr[a + j], ri[a + j], buf[j], buf[j - 1]));
     for (int k = a; k <= b; ++k) {
       const Field& R = buf[k - a];
-      WD_TRY(mhat(c, kappa, false, R, MR));
-      WD_TRY(mhat(c, kappa, false, L, ML));
-      WD_TRY(mhat_outer(c, kappa, MR, L, coef * scale, F));
-      WD_TRY(mhat_outer(c, kappa, ML, R, coef * scale, F));
+      // Lo = D_oe L, ML = M_hat L, MLo = D^dag_oe ML (the odd halves of L~ and
+      // (M L)~), and the same for R: six hops, each used twice below
+      WD_TRY(hop(c, 1, false, L, Lo, nullptr, 0.0, false, false));
+      WD_TRY(hop(c, 0, false, Lo, ML, &L, -k2, false, false));
+      WD_TRY(hop(c, 1, true, ML, MLo, nullptr, 0.0, false, false));
+      WD_TRY(hop(c, 1, false, R, Ro, nullptr, 0.0, false, false));
+      WD_TRY(hop(c, 0, false, Ro, MR, &R, -k2, false, false));
+      WD_TRY(hop(c, 1, true, MR, MRo, nullptr, 0.0, false, false));
+      // Re((M R)~^dag dD L~) and Re((M L)~^dag dD R~), one pass over the links
+      const double cf[2] = {-coef * scale * k2, -coef * scale * k2};
+      const Field Ye[2] = {MR, ML}, Yo[2] = {MRo, MLo}, Xe[2] = {L, R}, Xo[2] = {Lo, Ro};
+      WD_TRY(force_outer2(c, cf, Ye, Yo, Xe, Xo, F));
       if (k < m - 1) {
-        WD_TRY(k_minus(c, kappa, rr[k], -ri[k], L, Ln));
+        // K L = M^dag (M L) = ML - kappa^2 D^dag_eo MLo: one more hop
+        WD_TRY(hop(c, 0, true, MLo, Ln, &ML, -k2, false, false));
+        c->nmat += 1;
+        WD_TRY(caxpby(c, 1.0, 0.0, Ln, -rr[k], ri[k], L, Ln));   // (K - conj r_k) L
         std::swap(L, Ln);
       }
     }

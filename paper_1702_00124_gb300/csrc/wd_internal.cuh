@@ -549,6 +549,8 @@ int gaussian_draw_k(wd_ctx* c, int what, int parity, uint64_t seed, uint64_t str
 // force layer (force.cu)
 int force_outer(wd_ctx* c, double coef, const Field& Ye, const Field& Yo, const Field& Xe,
                 const Field& Xo, double* F, int prec);
+int force_outer2(wd_ctx* c, const double coef[2], const Field* Ye, const Field* Yo, const Field* Xe,
+                 const Field* Xo, double* F);
 
 // polynomial helpers (host)
 struct PolyCoef {
