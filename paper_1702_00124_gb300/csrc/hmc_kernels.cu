@@ -46,17 +46,23 @@ __device__ __forceinline__ void cayley_hamilton_exp(const cpx<double> (&Q)[9], c
   } else {
     const bool neg = c0 < 0;
     const double c0a = fabs(c0);
-    const double c0max = 2.0 * pow(c1 / 3.0, 1.5);
+    const double t3 = c1 / 3.0;
+    const double st3 = sqrt(t3);                   // sqrt(c1/3)
+    const double c0max = 2.0 * t3 * st3;           // 2 (c1/3)^{3/2}
     double r = c0a / c0max;
     r = r > 1.0 ? 1.0 : r;
     const double th = acos(r);
-    const double u = sqrt(c1 / 3.0) * cos(th / 3.0);
-    const double w = sqrt(c1) * sin(th / 3.0);
+    double s3, c3;
+    sincos(th / 3.0, &s3, &c3);
+    const double u = st3 * c3;
+    const double w = 1.7320508075688772935 * st3 * s3;   // sqrt(c1) sin(th/3)
     const double u2 = u * u, w2 = w * w;
-    const double xi0 = fabs(w) < 0.05 ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sin(w) / w;
-    const double cw = cos(w);
-    const cpx<double> e2 = mk(cos(2 * u), sin(2 * u));
-    const cpx<double> em = mk(cos(u), -sin(u));
+    double sw, cw, su, cu;
+    sincos(w, &sw, &cw);
+    sincos(u, &su, &cu);
+    const double xi0 = fabs(w) < 0.05 ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sw / w;
+    const cpx<double> e2 = mk(cu * cu - su * su, 2.0 * su * cu);   // exp(2iu)
+    const cpx<double> em = mk(cu, -su);                              // exp(-iu)
     const cpx<double> h0 = (u2 - w2) * e2 + em * mk(8 * u2 * cw, 2 * u * (3 * u2 + w2) * xi0);
     const cpx<double> h1 = (2 * u) * e2 - em * mk(2 * u * cw, -(3 * u2 - w2) * xi0);
     const cpx<double> h2 = e2 - em * mk(cw, 3 * u * xi0);

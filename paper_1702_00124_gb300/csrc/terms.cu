@@ -130,8 +130,18 @@ static int poly_force(wd_ctx* c, double kappa, const std::vector<double>& rr, co
   return WD_OK;
 }
 
-// C^dag v = sqrt(c) prod_{k<=n/2} (K - conj z_k) v
+// C^dag v = sqrt(c) prod_{k<=n/2} (K - conj z_k) v (FP64 fields; the factors in
+// double-float when the context selects it for FP64-accurate operators)
 static int apply_cdag(wd_ctx* c, double kappa, const PolyCoef& pc, const Field& v, const Field& out) {
+  if (c->resid_dd && c->gauge_dd) {
+    WsGuard w(c);
+    Field a;
+    WD_TRY(w.get(WD_DD, &a));
+    WD_TRY(convert(c, v, a));
+    WD_TRY(axpby(c, std::sqrt(pc.scale), a, 0.0, a, a));
+    for (int k = 0; k < pc.n / 2; ++k) WD_TRY(k_minus(c, kappa, pc.zr[k], -pc.zi[k], a, a));
+    return convert(c, a, out);
+  }
   WD_TRY(axpby(c, std::sqrt(pc.scale), v, 0.0, v, out));
   for (int k = 0; k < pc.n / 2; ++k) WD_TRY(k_minus(c, kappa, pc.zr[k], -pc.zi[k], out, out));
   return WD_OK;
@@ -141,6 +151,31 @@ static int solve(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, c
                  const wd_cg_params& p) {
   wd_cg_info info;
   return cg_solve_f(c, kappa, filt, b, x, p, &info, true);
+}
+
+// FP64-accurate operator applications on FP64 fields for the actions and the
+// heat bath: in FP64, or in double-float when the context selects it for its
+// residuals (the same accuracy class, about 1e-13 relative).
+static int poly_apply_hp(wd_ctx* c, double kappa, const wd_poly& P, const Field& in, const Field& out) {
+  if (!(c->resid_dd && c->gauge_dd)) return poly_apply_f(c, kappa, P, WD_F64, in, out);
+  WsGuard w(c);
+  Field a, b;
+  WD_TRY(w.get(WD_DD, &a));
+  WD_TRY(w.get(WD_DD, &b));
+  WD_TRY(convert(c, in, a));
+  WD_TRY(poly_apply_f(c, kappa, P, WD_DD, a, b));
+  return convert(c, b, out);
+}
+
+static int khat_hp(wd_ctx* c, double kappa, const Field& in, const Field& out) {
+  if (!(c->resid_dd && c->gauge_dd)) return khat_any(c, kappa, in, out);
+  WsGuard w(c);
+  Field a, b;
+  WD_TRY(w.get(WD_DD, &a));
+  WD_TRY(w.get(WD_DD, &b));
+  WD_TRY(convert(c, in, a));
+  WD_TRY(khat_any(c, kappa, a, b));
+  return convert(c, b, out);
 }
 
 // S of one term; when Xo / Yo are given, also the solution X = A^-1 psi and
@@ -168,7 +203,7 @@ int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_param
       return WD_OK;
     }
     case WD_TERM_POLY: {
-      WD_TRY(poly_apply_f(c, t.kappa, t.poly, WD_F64, phi, AX));
+      WD_TRY(poly_apply_hp(c, t.kappa, t.poly, phi, AX));
       WD_TRY(dot(c, phi, AX, &re, nullptr));
       *S = re;
       return WD_OK;
@@ -176,8 +211,8 @@ int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_param
     case WD_TERM_FILTERED: {
       WD_TRY(w.get(WD_F64, &tmp));
       WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
-      WD_TRY(poly_apply_f(c, t.kappa, t.poly, WD_F64, X, tmp));
-      WD_TRY(khat_any(c, t.kappa, tmp, AX));
+      WD_TRY(poly_apply_hp(c, t.kappa, t.poly, X, tmp));
+      WD_TRY(khat_hp(c, t.kappa, tmp, AX));
       WD_TRY(dot(c, phi, X, &re, nullptr));
       WD_TRY(dot(c, X, AX, &xax, nullptr));
       *S = 2.0 * re - xax;
