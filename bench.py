@@ -433,7 +433,14 @@ def main():
                 "clocks": clk,
                 "trajectory": {"dH": [float(r["dH"]) for r in timed], "accepted": acc,
                                "n_mat_per_traj": nmat, "force_evals": [r["n_force_evals"] for r in timed],
-                               "integrator_ops": len(ops)},
+                               "integrator_ops": len(ops),
+                               # device time per phase of the last timed trajectory (ms)
+                               "phases_ms": {"heatbath": timed[-1]["t_heatbath_ms"],
+                                             "hamiltonians": timed[-1]["t_hamiltonian_ms"],
+                                             "T_steps": timed[-1]["t_T_ms"],
+                                             "gauge_force": timed[-1]["t_gauge_force_ms"],
+                                             "force_filtered_and_hasenbusch": timed[-1]["t_force_group_ms"][0],
+                                             "force_poly": timed[-1]["t_force_group_ms"][1]}},
                 "breakdown": extras,
                 "autotuned_hop_shapes": {str(k): list(v) for k, v in lat.tuned().items()}}
         print(json.dumps(line))

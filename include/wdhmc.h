@@ -250,6 +250,11 @@ typedef struct {
   int accepted;
   long long n_mat;           /* K_hat applications in the trajectory */
   int n_force_evals;
+  /* device time (CUDA events on the context stream), ms: heat bath and
+   * momenta, the two Hamiltonians, all T steps, the gauge force, and the
+   * fermion forces of integrator groups 0..3 */
+  double t_heatbath_ms, t_hamiltonian_ms, t_T_ms, t_gauge_force_ms;
+  double t_force_group_ms[4];
 } wd_hmc_result;
 
 /* Heat bath, momentum draw, integration, accept/reject with uniform u (host).

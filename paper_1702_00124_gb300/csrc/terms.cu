@@ -581,12 +581,26 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   Field chi;
   WD_TRY(w.get(WD_F64, &chi));
   for (auto& f : phi) WD_TRY(w.get(WD_F64, &f));
+  // phase timing: (phase, start, stop) events on the context stream, read at the end
+  enum { PH_HB = 0, PH_H, PH_T, PH_GF, PH_F0 };
+  struct Mark { int phase; cudaEvent_t e0, e1; };
+  std::vector<Mark> marks;
+  auto begin = [&](int phase) {
+    Mark m{phase, nullptr, nullptr};
+    cudaEventCreate(&m.e0);
+    cudaEventCreate(&m.e1);
+    cudaEventRecord(m.e0, c->stream);
+    marks.push_back(m);
+  };
+  auto end = [&]() { cudaEventRecord(marks.back().e1, c->stream); };
   // momenta and pseudofermions
+  begin(PH_HB);
   WD_TRY(gaussian_draw_k(c, 1, 0, p->seed, base, c->mom));
   for (int i = 0; i < p->nterms; ++i) {
     WD_TRY(gaussian_draw_k(c, 0, 0, p->seed, base + 1 + i, (double*)chi.data));
     WD_TRY(term_heatbath(c, p->terms[i], chi, p->cg_acc, phi[i]));
   }
+  end();
   auto hamiltonian = [&](double* H, double* SG) -> int {
     double k, s, sum;
     WD_TRY(kinetic_k(c, c->mom, &k));
@@ -604,26 +618,36 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
     *H = sum;
     return WD_OK;
   };
+  begin(PH_H);
   WD_TRY(hamiltonian(&res->H0, &res->S_gauge0));
+  end();
   int nf = 0;
   const int fprec = p->force_prec == WD_F64 ? WD_F64 : WD_F32;
   for (int k = 0; k < p->nops; ++k) {
     const wd_op& o = p->ops[k];
     if (o.kind == 0) {
+      begin(PH_T);
       WD_TRY(step_T_k(c, c->mom, o.eps));
+      end();
     } else {
       if (o.group == -1 && p->beta > 0) {
+        begin(PH_GF);
         WD_TRY(gauge_force_k(c, p->beta, fprec, -o.eps, c->mom));
+        end();
         ++nf;
       }
       for (int i = 0; i < p->nterms; ++i) {
         if (p->term_group[i] != o.group) continue;
+        begin(o.group >= 0 && o.group < 4 ? PH_F0 + o.group : PH_GF);
         WD_TRY(term_force(c, p->terms[i], phi[i], md, -o.eps, c->mom));
+        end();
         ++nf;
       }
     }
   }
+  begin(PH_H);
   WD_TRY(hamiltonian(&res->H1, &res->S_gauge1));
+  end();
   res->dH = res->H1 - res->H0;
   res->n_force_evals = nf;
   int acc = 0;
@@ -636,6 +660,18 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   }
   res->n_mat = c->nmat - nmat0;
   WD_CUDA(cudaStreamSynchronize(c->stream));
+  double t[PH_F0 + 4] = {0};
+  for (auto& m : marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.e0, m.e1) == cudaSuccess) t[m.phase] += ms;
+    cudaEventDestroy(m.e0);
+    cudaEventDestroy(m.e1);
+  }
+  res->t_heatbath_ms = t[PH_HB];
+  res->t_hamiltonian_ms = t[PH_H];
+  res->t_T_ms = t[PH_T];
+  res->t_gauge_force_ms = t[PH_GF];
+  for (int g = 0; g < 4; ++g) res->t_force_group_ms[g] = t[PH_F0 + g];
   return WD_OK;
 }
 

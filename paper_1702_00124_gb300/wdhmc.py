@@ -61,7 +61,9 @@ class wd_hmc_params(C.Structure):
 class wd_hmc_result(C.Structure):
     _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("dH", C.c_double), ("S_gauge0", C.c_double),
                 ("S_gauge1", C.c_double), ("accepted", C.c_int), ("n_mat", C.c_longlong),
-                ("n_force_evals", C.c_int)]
+                ("n_force_evals", C.c_int), ("t_heatbath_ms", C.c_double), ("t_hamiltonian_ms", C.c_double),
+                ("t_T_ms", C.c_double), ("t_gauge_force_ms", C.c_double),
+                ("t_force_group_ms", C.c_double * 4)]
 
 
 _P = C.c_void_p
@@ -370,7 +372,9 @@ class Lattice:
                           traj_index)
         r = wd_hmc_result()
         _check(lib.hmc_trajectory(self.h, C.byref(p), u, C.byref(r)))
-        return {k: getattr(r, k) for k, _ in wd_hmc_result._fields_}
+        out = {k: getattr(r, k) for k, _ in wd_hmc_result._fields_}
+        out["t_force_group_ms"] = list(r.t_force_group_ms)
+        return out
 
     def wd_nmat(self, reset=False):
         n = C.c_longlong(0)
