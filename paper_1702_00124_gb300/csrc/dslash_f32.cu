@@ -12,4 +12,63 @@ int hop_f32(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out,
   return hop_with_gauge<float>(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg, false);
 }
 
+// Last hop of K_hat fused with the Chebyshev recurrence step (FP32):
+//   Ks = y + alpha D^dag_eo x  (y = M_hat s, x = D^dag_oe y),
+//   out = ca (v + cmu s - Ks) - cb sprev.
+// Saves the K s vector and the separate 5-vector pass of the step kernel.
+template <class G>
+__global__ void __launch_bounds__(128) k_hop_poly(HopArgs<SpF32, SpF32, SpF32, G> a, SpF32 v, SpF32 s, SpF32 sp,
+                                                  float ca, float cmu, float cb) {
+  const long cb_ = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb_ >= a.g.Vh) return;
+  int c[4];
+  a.g.coords(cb_, 0, c);
+  cpx<float> acc[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) acc[j] = mk<float>(0, 0);
+  hop_dir<0, true>(a.g, 0, cb_, c, a.in, a.gauge, acc);
+  hop_dir<1, true>(a.g, 0, cb_, c, a.in, a.gauge, acc);
+  hop_dir<2, true>(a.g, 0, cb_, c, a.in, a.gauge, acc);
+  hop_dir<3, true>(a.g, 0, cb_, c, a.in, a.gauge, acc);
+  cpx<float> yv[12], q[12];
+  a.y.loadT(cb_, yv);
+  const float al = (float)a.alpha;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];   // K s
+  v.loadT(cb_, yv);
+  s.loadT(cb_, q);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) yv[j] = yv[j] + cmu * q[j] - acc[j];
+  sp.loadT(cb_, q);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) yv[j] = ca * yv[j] - cb * q[j];
+  a.out.store(cb_, yv);
+}
+
+// out = ca (v + cmu s - K_hat s) - cb sprev for FP32 fields (t1, t2 scratch)
+int khat_poly_step_f32(wd_ctx* c, double kappa, const Field& s, Field& t1, Field& t2, const Field& v,
+                       const Field& sprev, double ca, double cmu, double cb, const Field& out) {
+  const Field* fields[] = {&s, &t1, &t2, &v, &sprev, &out};
+  for (const Field* f : fields)
+    if (f->fmt != WD_F32) return fail(WD_ERR_ARG, "khat_poly_step_f32: FP32 fields only");
+  const double a2 = -kappa * kappa;
+  WD_TRY(hop(c, 1, false, s, t1, nullptr, 0.0, false, false));
+  WD_TRY(hop(c, 0, false, t1, t2, &s, a2, false, false));
+  WD_TRY(hop(c, 1, true, t2, t1, nullptr, 0.0, false, false));
+  const int nb = nblocks(c->g.Vh, 128);
+  if (c->recon == WD_RECON_12) {
+    HopArgs<SpF32, SpF32, SpF32, GF32R12> a{c->g, 0, sp32(t1), sp32(out), sp32(t2), GF32R12{c->gauge32r12, c->g.Vh},
+                                            a2, reducer(c), nullptr};
+    k_hop_poly<<<nb, 128, 0, c->stream>>>(a, sp32(v), sp32(s), sp32(sprev), (float)ca, (float)cmu, (float)cb);
+  } else {
+    HopArgs<SpF32, SpF32, SpF32, GF32> a{c->g, 0, sp32(t1), sp32(out), sp32(t2), GF32{c->gauge32, c->g.Vh}, a2,
+                                         reducer(c), nullptr};
+    k_hop_poly<<<nb, 128, 0, c->stream>>>(a, sp32(v), sp32(s), sp32(sprev), (float)ca, (float)cmu, (float)cb);
+  }
+  WD_CHECK_LAUNCH();
+  c->prof.all[WD_F32] += 1;
+  c->nmat += 1;
+  return WD_OK;
+}
+
 }  // namespace wd

@@ -87,9 +87,14 @@ int poly_apply_f(wd_ctx* c, double kappa, const wd_poly& P, int /*prec*/, const 
   WD_TRY(zero(c, sp));                         // s_0 = 0
   WD_TRY(axpby(c, pc.s1, in, 0.0, in, s));     // s_1 = v / mu
   for (int k = 1; k <= P.n; ++k) {
-    WD_TRY(apply_khat(c, kappa, s, ks, t1, t2, false, false));
     const Field& dst = (k == P.n) ? out : sp;  // s_{k+1} overwrites s_{k-1}
-    WD_TRY(poly_step(c, pc.a[k], pc.mu, pc.b[k], in, s, ks, sp, dst));
+    if (f == WD_F32) {
+      // FP32: the step is fused into the last hop of K_hat
+      WD_TRY(khat_poly_step_f32(c, kappa, s, t1, t2, in, sp, pc.a[k], pc.mu, pc.b[k], dst));
+    } else {
+      WD_TRY(apply_khat(c, kappa, s, ks, t1, t2, false, false));
+      WD_TRY(poly_step(c, pc.a[k], pc.mu, pc.b[k], in, s, ks, sp, dst));
+    }
     if (k < P.n) std::swap(s, sp);
   }
   return WD_OK;

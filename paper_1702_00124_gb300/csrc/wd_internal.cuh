@@ -509,6 +509,8 @@ int apply_mhat(wd_ctx* c, double kappa, bool dag, const Field& in, const Field& 
 int apply_khat(wd_ctx* c, double kappa, const Field& in, const Field& out, Field& t1, Field& t2,
                bool norm_cg, bool in_cg = false);
 double hop_bytes(int fmt_in, int fmt_out, bool xpay, int gauge_bytes_per_link, long Vh);
+int khat_poly_step_f32(wd_ctx* c, double kappa, const Field& s, Field& t1, Field& t2, const Field& v,
+                       const Field& sprev, double ca, double cmu, double cb, const Field& out);
 
 // blas layer (blas.cu)
 int convert(wd_ctx* c, const Field& in, const Field& out);
