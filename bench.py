@@ -168,6 +168,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def max_over_ranks(seconds, dist, device):
+    """Slowest rank's timed region (every rank runs an independent replica)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world, steps, t_max):
+    """Whole-job trajectories per second: all ranks' trajectories / slowest rank."""
+    return world * steps / t_max
+
+
 def batched_workload_run(wd):
     """The batched workload: 24 lattices (8 x 8^4, 8 x 12^3 x 24, 8 x 16^3 x 32),
     links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian right-hand sides
@@ -217,13 +233,18 @@ def kernel_case(args):
     U_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda")
     lat.wd_gauge_load(U_dev)
     del U_dev
+    lat.wd_set_autotune(0)     # the default launch shape, as production settles on
     prec, recon = {"khat_f32_recon12": (wd.F32, 1), "khat_bf16_recon12": (wd.BF16, 1),
-                   "khat_f64": (wd.F64, 0), "khat_df": (wd.DF, 0)}[args.kernel_case]
+                   "khat_f64": (wd.F64, 0), "khat_df": (wd.DF, 0),
+                   "poly_f32_recon12": (wd.F32, 1)}[args.kernel_case]
     lat.wd_set_recon(recon)
     x, y = lat.half_spinor(), lat.half_spinor()
     lat.gaussian_draw(0, 0, 1, 1, x)
     for _ in range(args.reps):
-        lat.mdagm_apply(w["kappa"], prec, 1, x, y)
+        if args.kernel_case.startswith("poly"):
+            lat.poly_filter_apply(w["kappa_h"], (4, w["poly"][1], w["poly"][2]), prec, x, y)
+        else:
+            lat.mdagm_apply(w["kappa"], prec, 1, x, y)
     torch.cuda.synchronize()
     lat.close()
     print(f"kernel case {args.kernel_case} on {args.workload}: {args.reps} K_hat applications")
@@ -237,7 +258,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-vs-FP64 and e2e measurements")
-    ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64", "khat_df"],
+    ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64", "khat_df",
+                                              "poly_f32_recon12"],
                     help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
     ap.add_argument("--reps", type=int, default=4)
     args = ap.parse_args()
@@ -319,14 +341,9 @@ def main():
             shares[name] = {"launches": n, "avg_ms": pr["ms"] / pr["launches"],
                             "share": n * pr["ms"] / pr["launches"] / (elapsed * 1e3)}
     clk = clocks.stop()
-    t_max = elapsed
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        dist.barrier()
+    t_max = max_over_ranks(elapsed, dist, "cuda")
     timed = results[-args.steps:]
-    value = world * args.steps / t_max
+    value = replica_throughput(world, args.steps, t_max)
 
     hbm, peak_kind = peaks()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else None
