@@ -135,6 +135,58 @@ def test_gaussian_draws(setup):
         assert np.max(np.abs(gu.unpack(lat, h, par) - ref)) < 1e-13
 
 
+def test_bench_configuration_trajectory():
+    """The bench's configuration at 4^4: PF-MP + gauge, nested Omelyan 2MN with the
+    bench's level structure, FP32 forces, mixed-precision solves to 1e-10 with
+    double-float residuals, 12-real FP32 links.  dH must agree with the oracle's FP64
+    trajectory to 1e-4 + 1e-4 |dH| (FP32 forces move the trajectory by ~1e-6)."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 4)
+    U0 = synthetic.gauge_field(dims, 0.3, 951)
+    k, kh, beta, tau = 0.124, 0.115, 5.6, 0.5
+    poly = (8, 0.02, 6.0)
+    seed, traj = 321, 2
+    pf = ChebyshevFilter(*poly)
+    terms_o = [actions.term("poly", kh, poly=pf), actions.term("filtered", kh, poly=pf),
+               actions.term("hasenbusch", k, kh)]
+    terms_g = [wd.term(wd.POLY, kh, poly=poly), wd.term(wd.FILTERED, kh, poly=poly),
+               wd.term(wd.HASENBUSCH, k, kh)]
+    groups = [1, 0, 0]
+    levels = [(0, 3), (1, 1), (-1, 2)]
+    V = int(np.prod(dims))
+    base = traj * 64
+    P0 = philox.gaussian_field(V * 32, seed, base).reshape(lattice.shape(dims) + (4, 8))
+    phis = []
+    for i, t in enumerate(terms_o):
+        g = philox.gaussian_field(V * 24, seed, base + 1 + i)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        phis.append(actions.heatbath(U0, t, chi))
+
+    def H(U, P):
+        return hmc.kinetic(P) + force.gauge_action(U, beta) + sum(
+            actions.action(U, t, ph)[0] for t, ph in zip(terms_o, phis))
+
+    def fog(grp, U):
+        if grp == -1:
+            return force.gauge_force(U, beta)
+        return sum(force.fermion_force(U, t, ph) for t, ph, g in zip(terms_o, phis, groups) if g == grp)
+
+    U1, P1 = hmc.integrate(U0, P0, hmc.nested(levels, tau, "omelyan"), fog)
+    dH_ref = H(U1, P1) - H(U0, P0)
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U0))
+    lat.wd_set_recon(wd.RECON_12)
+    lat.wd_set_residual(1)
+    ops = wd.wd_schedule_nested(1, tau, [g for g, _ in levels], [n for _, n in levels])
+    p32 = wd.cg_params(tol=1e-10, prec=wd.F32, maxiter=20000)
+    r = lat.hmc_trajectory(terms_g, groups, beta, ops, p32, p32, wd.F32, seed, traj, 0.0)
+    assert abs(r["dH"] - dH_ref) < 1e-4 + 1e-4 * abs(dH_ref), (r["dH"], dH_ref)
+    assert r["t_force_group_ms"][0] > 0 and r["t_T_ms"] > 0
+    lat.close()
+
+
 def test_trajectory_matches_oracle():
     """One PF-MP + gauge trajectory with a nested Omelyan 2MN schedule, every
     step in FP64: same draws (Philox), same schedule structure (the GPU merges
