@@ -8,6 +8,7 @@ even-site operator K_hat(kappa) = M_hat^dag M_hat:
   hasenbusch  S = phi^dag M_h K^-1 M_h^dag phi           (Section 2, "phi^dag J K^-1 phi")
   poly        S = phi^dag P(K) phi                       (Section 2, polynomial filter S_1)
   filtered    S = phi^dag [P(K) K]^-1 phi                (Section 2, filtered S_2)
+  ratio       S = phi^dag Q(K) phi, Q = P_hi / P_lo      (Section 3.3, S_2PF middle term)
 
 Readings of the paper:
   * "phi^dag J K^-1 phi" (Sections 2 and 4.1) is not Hermitian as printed; it
@@ -19,7 +20,10 @@ Readings of the paper:
     of Section 4.1 is read as the same heavier-mass condition.
 Composite actions: 1MP = [plain(k'), hasenbusch(k, k')]; 1PF = [poly(k), filtered(k)];
 2MP = [plain(k1), hasenbusch(k2, k1), hasenbusch(k, k2)];
-PF-MP (Section 4.1) = [poly(k'), filtered(k'), hasenbusch(k, k')].
+PF-MP (Section 4.1) = [poly(k'), filtered(k'), hasenbusch(k, k')];
+2PF (Section 3.3) = [poly(P_1, k), ratio(P_2/P_1, k), filtered(P_2, k)];
+1PF-2MP (Section 4.2) = [poly(k1), filtered(k1), hasenbusch(k2, k1), hasenbusch(k, k2)];
+2PF-1MP (Section 4.2) = [poly(P_1, k'), ratio(P_2/P_1, k'), filtered(P_2, k'), hasenbusch(k, k')].
 
 Heat bath (Section 2: phi is drawn from exp(-S_F) by way of Gaussian chi,
 exp(-chi^dag chi)); each phi below makes S(phi) = chi^dag chi:
@@ -63,7 +67,7 @@ def action(U, t, phi, tol=1e-14):
         psi = wilson.apply_Mhat(U, phi, t["kappa_h"], dagger=True)
         X, info = cg(K, psi, tol)
         return vdot(psi, X).real, dict(X=X, info=info)
-    if k == "poly":
+    if k in ("poly", "ratio"):
         return vdot(phi, t["poly"].apply(K, phi)).real, {}
     if k == "filtered":
         X, info = cg(filtered_op(U, t["kappa"], t["poly"]), phi, tol)
@@ -82,7 +86,7 @@ def heatbath(U, t, chi, tol=1e-14):
         w, _ = cg(K_op(U, t["kappa_h"]), y, tol)
         return wilson.apply_Mhat(U, w, t["kappa_h"])
     K = K_op(U, kap)
-    if k == "poly":
+    if k in ("poly", "ratio"):
         y = t["poly"].apply_half(K, chi, dagger=True)
         phi, _ = cg(lambda v: t["poly"].apply(K, v), y, tol)
         return phi

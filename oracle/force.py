@@ -88,7 +88,7 @@ def fermion_force(U, t, phi, tol=1e-14):
             F = F + 2 * _dre_mhat(U, phi, X, t["kappa_h"])
         return F
     p = t["poly"]
-    if k == "poly":
+    if k in ("poly", "ratio"):
         return poly_force(U, kap, p.roots(), p.scale(), phi)
     if k == "filtered":
         X, _ = cg(filtered_op(U, kap, p), phi, tol)

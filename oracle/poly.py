@@ -92,3 +92,68 @@ class ChebyshevFilter:
     def roots_times_x(self):
         """Roots of x P(x): {0} and z_k, with the same scale c."""
         return np.concatenate([[0.0 + 0.0j], self.roots()])
+
+
+class RatioFilter:
+    """Q = P_hi / P_lo for two filters on the same [eps, lam] (Section 3.3 of the
+    paper, two-filter action S_2PF, "Q(K) = P_2(K)/P_1(K)").  Q is a polynomial when
+    every root of P_lo is a root of P_hi, which for the reading above holds when
+    (n_lo + 1) divides (n_hi + 1); its roots are the remaining roots of P_hi and its
+    scale c_hi / c_lo.  Applied, like the filter, as the root product with conjugate
+    roots paired into real quadratics."""
+
+    def __init__(self, hi, lo):
+        assert hi.eps == lo.eps and hi.lam == lo.lam and (hi.n + 1) % (lo.n + 1) == 0
+        self.hi, self.lo = hi, lo
+        zl = lo.roots()
+        keep = [z for z in hi.roots() if np.min(np.abs(zl - z)) > 1e-9 * hi.lam]
+        self._roots = np.array(keep)
+        assert len(self._roots) == hi.n - lo.n
+        self.n = len(self._roots)
+
+    def roots(self):
+        return self._roots
+
+    def scale(self):
+        return self.hi.scale() / self.lo.scale()
+
+    def value(self, x):
+        return self.hi.value(x) / self.lo.value(x)
+
+    def value_product(self, x):
+        out = self.scale() * np.ones_like(np.asarray(x, dtype=np.complex128))
+        for z in self._roots:
+            out = out * (x - z)
+        return out
+
+    def _pairs(self):
+        """Indices pairing each root with its conjugate."""
+        z = self._roots
+        used, pairs = set(), []
+        for i in range(len(z)):
+            if i in used:
+                continue
+            j = int(np.argmin(np.abs(z - z[i].conj()) + np.where(np.arange(len(z)) == i, np.inf, 0)))
+            used.update((i, j))
+            pairs.append((i, j))
+        return pairs
+
+    def apply(self, K, v):
+        pairs = self._pairs()
+        f = self.scale() ** (1.0 / len(pairs))
+        out = v
+        for i, _ in pairs:
+            zi = self._roots[i]
+            Kv = K(out)
+            out = f * (K(Kv) - 2 * zi.real * Kv + abs(zi) ** 2 * out)
+        return out
+
+    def apply_half(self, K, v, dagger=False):
+        """D v with D = sqrt(scale) prod over one root of each conjugate pair, D^dag D = Q."""
+        z = np.array([self._roots[i] for i, _ in self._pairs()])
+        if dagger:
+            z = z.conj()
+        out = np.sqrt(self.scale()) * v
+        for zk in z:
+            out = K(out) - zk * out
+        return out

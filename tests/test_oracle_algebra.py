@@ -101,6 +101,24 @@ def test_root_subset_for_ratio_filter(p1, p2):
     assert contained == ((p2 + 1) % (p1 + 1) == 0)
 
 
+@pytest.mark.parametrize("lo,hi", [(4, 24), (4, 54), (2, 8)])
+def test_ratio_filter_is_polynomial(lo, hi):
+    """Q = P_hi / P_lo (Section 3.3): the root product of the leftover roots equals
+    the ratio of the two closed forms, and its roots come in conjugate pairs."""
+    from oracle.poly import RatioFilter
+    q = RatioFilter(ChebyshevFilter(hi, 0.005, 8.0), ChebyshevFilter(lo, 0.005, 8.0))
+    assert q.n == hi - lo
+    x = np.concatenate([np.linspace(0.005, 8.0, 101), [0.001, 12.0]])
+    closed = q.value(x)
+    prod = q.value_product(x)
+    assert np.max(np.abs(prod.imag)) < 1e-9 * np.max(np.abs(closed))
+    assert np.max(np.abs(prod.real - closed) / np.abs(closed)) < 1e-9
+    z = q.roots()
+    assert np.max([np.min(np.abs(z - w.conj())) for w in z]) < 1e-12
+    # as an operator: a diagonal "K" gives the scalar values
+    assert np.allclose(q.apply(lambda v: x * v, np.ones_like(x)), closed, rtol=1e-10)
+
+
 def test_filter_on_free_field_modes():
     dims = (4, 4, 4, 8)
     kappa = 0.12

@@ -22,11 +22,14 @@ LD = np.clongdouble
 
 
 def _terms(kappa, kappa_h, n=4):
+    from oracle.poly import RatioFilter
     pf = ChebyshevFilter(n, 0.05, 5.0)
+    q = RatioFilter(ChebyshevFilter(8, 0.05, 5.0), ChebyshevFilter(2, 0.05, 5.0))
     return [actions.term("plain", kappa),
             actions.term("hasenbusch", kappa, kappa_h),
             actions.term("poly", kappa_h, poly=pf),
-            actions.term("filtered", kappa_h, poly=pf)]
+            actions.term("filtered", kappa_h, poly=pf),
+            actions.term("ratio", kappa_h, poly=q)]
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +40,7 @@ def setup44():
     return dims, U, chi
 
 
-@pytest.mark.parametrize("i", range(4))
+@pytest.mark.parametrize("i", range(5))
 def test_heatbath_gives_chi_norm(setup44, i):
     dims, U, chi = setup44
     t = _terms(0.125, 0.115)[i]
@@ -46,7 +49,7 @@ def test_heatbath_gives_chi_norm(setup44, i):
     assert abs(S - vdot(chi, chi).real) < 1e-10 * vdot(chi, chi).real
 
 
-@pytest.mark.parametrize("i", range(4))
+@pytest.mark.parametrize("i", range(5))
 def test_gauge_invariance(setup44, i):
     dims, U, chi = setup44
     t = _terms(0.125, 0.115)[i]
@@ -86,6 +89,28 @@ def test_pfmp_determinant_identity():
     assert np.allclose(PJ, (v * pf.value(w)) @ v.conj().T, atol=1e-10 * np.abs(PJ).max())
 
 
+def test_2pf_determinant_identity():
+    """2PF (Section 3.3): det P_1^-1 . det Q^-1 . det(P_2 K) = det K with Q = P_2 / P_1."""
+    from oracle.poly import RatioFilter
+    dims = (2, 2, 2, 2)
+    U = synthetic.gauge_field(dims, 0.6, 52)
+    k = 0.12
+    p1, p2 = ChebyshevFilter(2, 0.02, 6.0), ChebyshevFilter(8, 0.02, 6.0)
+    q = RatioFilter(p2, p1)
+    shp = lattice.shape(dims) + (4, 3)
+    sup = np.broadcast_to((lattice.parity(dims) == 0)[..., None, None], shp)
+    D = lambda op: dense_matrix(op, sup)[0]
+    Kop = lambda w: wilson.apply_Khat(U, w, k)
+    K = D(Kop)
+    P1 = D(lambda v: p1.apply(Kop, v))
+    Q = D(lambda v: q.apply(Kop, v))
+    P2K = D(lambda v: p2.apply(Kop, Kop(v)))
+    logdet = lambda A: np.linalg.slogdet(A)[1]
+    lhs = -(logdet(P1) + logdet(Q) - logdet(P2K))
+    assert abs(lhs - logdet(K)) < 1e-9 * abs(logdet(K))
+    assert np.allclose(P1 @ Q, D(lambda v: p2.apply(Kop, v)), atol=1e-9 * np.abs(P1 @ Q).max())
+
+
 def _fd_check(U, action_of_U, F, links, h=1e-5, rtol=1e-9):
     ULD = U.astype(LD)
     T = su3.generators(LD)
@@ -114,7 +139,7 @@ def _links(dims, n, seed):
     return out
 
 
-@pytest.mark.parametrize("i", range(4))
+@pytest.mark.parametrize("i", range(5))
 def test_fermion_force_finite_difference(i):
     dims = (2, 2, 2, 4)
     U = synthetic.gauge_field(dims, 0.5, 61)
