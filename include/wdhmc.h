@@ -78,9 +78,16 @@ enum wd_recon { WD_RECON_18 = 0, WD_RECON_12 = 1 };
  *   HASENBUSCH  S = phi^dag M_h K^-1 M_h^dag phi,  M_h = M_hat(kappa_h), kappa_h < kappa
  *               (the Hermitian reading of the printed phi^dag J K^-1 phi)
  *   POLY        S = phi^dag P(K) phi
- *   FILTERED    S = phi^dag [P(K) K]^-1 phi                                 */
+ *   FILTERED    S = phi^dag [P(K) K]^-1 phi
+ *   RATIO       S = phi^dag Q(K) phi, Q = P / P_lo (Section 3.3, the middle term of
+ *               the two-filter action); Q is a polynomial when (n_lo + 1) divides
+ *               (n + 1) on the same [eps, lam]: its roots are those of P whose index k
+ *               is not a multiple of (n + 1) / (n_lo + 1), its scale c / c_lo.
+ * Composite actions: 1MP, 2MP, PF-MP, 1PF-2MP from PLAIN / HASENBUSCH / POLY /
+ * FILTERED; 2PF = [POLY(P_1), RATIO(P_2 / P_1), FILTERED(P_2)]; 2PF-1MP adds a
+ * HASENBUSCH term (Section 4.2). */
 enum wd_term_kind { WD_TERM_PLAIN = 0, WD_TERM_HASENBUSCH = 1, WD_TERM_POLY = 2,
-                    WD_TERM_FILTERED = 3 };
+                    WD_TERM_FILTERED = 3, WD_TERM_RATIO = 4 };
 
 /* Chebyshev filter P of even degree n approximating 1/x on [eps, lam]
  * (Section 2: "Chebyshev polynomials ... order p").  Reading: the minimax
@@ -92,7 +99,8 @@ typedef struct {
   int kind;          /* enum wd_term_kind */
   double kappa;      /* operator K = K_hat(kappa) */
   double kappa_h;    /* heavy kappa of a HASENBUSCH term */
-  wd_poly poly;      /* POLY / FILTERED */
+  wd_poly poly;      /* POLY / FILTERED; the numerator P of RATIO */
+  wd_poly poly_lo;   /* RATIO: the denominator P_lo */
 } wd_term;
 
 typedef struct {
@@ -194,13 +202,13 @@ int fermion_force(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_
  * without re-solving): X = A^-1 psi (psi = phi, or M_h^dag phi for
  * HASENBUSCH; A = K_hat, or K_hat P(K_hat) for FILTERED) and, for PLAIN and
  * HASENBUSCH, Y = M_hat X.  X and Y are caller half spinors or NULL (not
- * written for POLY / not needed). */
+ * written for POLY and RATIO / not needed). */
 int pf_action_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
                  double* S, double* X, double* Y);
 /* F += coef * dS/dw from the X (and Y) of pf_action_xy: the adjoint of the
  * action without a solve (Section 2, fermion force; only X and Y are kept per
  * term, polynomial-term vectors are recomputed).  Y may be NULL (formed from
- * X); POLY needs neither.  prec: WD_F64 or WD_F32 arithmetic. */
+ * X); POLY and RATIO need neither.  prec: WD_F64 or WD_F32 arithmetic. */
 int fermion_force_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const double* X,
                      const double* Y, int prec, double coef, double* F);
 /* Wilson plaquette action S_G = beta sum (1 - Re tr U_p / 3); *S host. */

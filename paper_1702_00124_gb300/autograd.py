@@ -40,7 +40,7 @@ class PFAction(torch.autograd.Function):
         lat = ctx.lat
         F = lat.algebra_field()
         kind = ctx.term.kind
-        lat.fermion_force_xy(ctx.term, ctx.phi, None if kind == wd.POLY else X,
+        lat.fermion_force_xy(ctx.term, ctx.phi, None if kind in (wd.POLY, wd.RATIO) else X,
                              Y if kind in (wd.PLAIN, wd.HASENBUSCH) else None, ctx.force_prec,
                              float(gS), F)
         return F, None, None, None, None, None

@@ -60,6 +60,68 @@ int poly_coef(const wd_poly& P, PolyCoef* out) {
   return WD_OK;
 }
 
+// Q = P_hi / P_lo on one interval (Section 3.3).  With th_k = 2 pi k / (n + 1)
+// the roots of P_lo are the roots of P_hi whose index k is a multiple of
+// m = (n_hi + 1) / (n_lo + 1); Q keeps the others, in ascending k, and has
+// scale c_hi / c_lo.  The kept set is closed under k -> n_hi + 1 - k (the
+// conjugate root), so its first half holds one root of every conjugate pair.
+int ratio_coef(const wd_poly& hi, const wd_poly& lo, PolyCoef* out) {
+  PolyCoef ph, pl;
+  WD_TRY(poly_coef(hi, &ph));
+  WD_TRY(poly_coef(lo, &pl));
+  if (hi.eps != lo.eps || hi.lam != lo.lam) return fail(WD_ERR_ARG, "ratio: both filters need the same [eps, lam]");
+  if (lo.n > hi.n || (hi.n + 1) % (lo.n + 1) != 0)
+    return fail(WD_ERR_ARG, "ratio: (n_lo + 1) must divide (n + 1)");
+  const int m = (hi.n + 1) / (lo.n + 1);
+  PolyCoef& c = *out;
+  c.n = hi.n - lo.n;
+  c.mu = ph.mu;
+  c.nu = ph.nu;
+  c.scale = ph.scale / pl.scale;
+  c.s1 = 0.0;
+  c.a.clear();
+  c.b.clear();
+  c.zr.clear();
+  c.zi.clear();
+  for (int k = 1; k <= hi.n; ++k) {
+    if (k % m == 0) continue;
+    c.zr.push_back(ph.zr[k - 1]);
+    c.zi.push_back(ph.zi[k - 1]);
+  }
+  return WD_OK;
+}
+
+// out = Q(K) in = prod_pairs f (K^2 - 2 Re z K + |z|^2) in, f = scale^(1/pairs).
+// Each factor is one recurrence-shaped update a (v + mu s - K s) - b s' with
+// v = s' = x, s = K x: a = -f, mu = 2 Re z, b = -f (1 + |z|^2); in FP32 it is
+// fused into the last hop of the second K.
+int roots_apply_f(wd_ctx* c, double kappa, const PolyCoef& q, const Field& in, const Field& out) {
+  const int f = in.fmt;
+  if (f != WD_F64 && f != WD_F32 && f != WD_DD) return fail(WD_ERR_ARG, "ratio: FP64, FP32 or double-float fields");
+  const int np = q.n / 2;
+  if (np == 0) return axpby(c, q.scale, in, 0.0, in, out);
+  const double fs = std::pow(q.scale, 1.0 / np);
+  WsGuard w(c);
+  Field s, ks, t1, t2;
+  WD_TRY(w.get(f, &s));
+  WD_TRY(w.get(f, &ks));
+  WD_TRY(w.get(f, &t1));
+  WD_TRY(w.get(f, &t2));
+  WD_TRY(convert(c, in, out));
+  for (int k = 0; k < np; ++k) {
+    const double zr = q.zr[k], zi = q.zi[k];
+    const double ca = -fs, cmu = 2.0 * zr, cb = -fs * (1.0 + zr * zr + zi * zi);
+    WD_TRY(apply_khat(c, kappa, out, s, t1, t2, false, false));
+    if (f == WD_F32) {
+      WD_TRY(khat_poly_step_f32(c, kappa, s, t1, t2, out, out, ca, cmu, cb, out));
+    } else {
+      WD_TRY(apply_khat(c, kappa, s, ks, t1, t2, false, false));
+      WD_TRY(poly_step(c, ca, cmu, cb, out, s, ks, out, out));
+    }
+  }
+  return WD_OK;
+}
+
 int khat_any(wd_ctx* c, double kappa, const Field& in, const Field& out) {
   WsGuard w(c);
   Field t1, t2;
@@ -102,12 +164,13 @@ int poly_apply_f(wd_ctx* c, double kappa, const wd_poly& P, int /*prec*/, const 
 
 // ----------------------------------------------------------------------------
 // operators for CG
-enum OpKind { OP_K = 0, OP_KP = 1, OP_P = 2 };
+enum OpKind { OP_K = 0, OP_KP = 1, OP_P = 2, OP_R = 3 };
 
 struct Op {
   OpKind kind;
   double kappa;
   wd_poly poly;
+  const PolyCoef* roots = nullptr;   // OP_R: Q in factored form
 };
 
 static int op_apply(wd_ctx* c, const Op& op, const Field& in, const Field& out, bool in_cg) {
@@ -122,6 +185,8 @@ static int op_apply(wd_ctx* c, const Op& op, const Field& in, const Field& out, 
   }
   if (op.kind == OP_P) {
     WD_TRY(poly_apply_f(c, op.kappa, op.poly, in.fmt, in, out));
+  } else if (op.kind == OP_R) {
+    WD_TRY(roots_apply_f(c, op.kappa, *op.roots, in, out));
   } else {
     Field s;
     WD_TRY(w.get(in.fmt, &s));
@@ -279,6 +344,13 @@ int cg_solve_poly(wd_ctx* c, double kappa, const wd_poly& P, const Field& b, con
   PolyCoef pc;
   WD_TRY(poly_coef(P, &pc));
   Op op{OP_P, kappa, P};
+  return cg_core(c, op, b, x, p, info, true);
+}
+
+// CG on Q(K_hat) (heat bath of the ratio term), from x = 0
+int cg_solve_ratio(wd_ctx* c, double kappa, const PolyCoef& q, const Field& b, const Field& x,
+                   const wd_cg_params& p, wd_cg_info* info) {
+  Op op{OP_R, kappa, wd_poly{0, 0, 0}, &q};
   return cg_core(c, op, b, x, p, info, true);
 }
 

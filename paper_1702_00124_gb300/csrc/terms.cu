@@ -7,7 +7,9 @@
 //   HASENBUSCH  S = phi^dag M_h K^-1 M_h^dag phi     phi = M_h J^-1 M^dag chi, J = K_hat(kappa_h)
 //   POLY        S = phi^dag P(K) phi                 phi = P^-1 C^dag chi, P = C^dag C
 //   FILTERED    S = phi^dag [P(K) K]^-1 phi          phi = C^dag M^dag chi
-// with C = sqrt(c) prod_{k <= n/2} (K - z_k).  Actions use the variational
+//   RATIO       S = phi^dag Q(K) phi, Q = P / P_lo   phi = Q^-1 D^dag chi, Q = D^dag D
+// with C = sqrt(c) prod_{k <= n/2} (K - z_k) and D the same product over the
+// first half of Q's roots (Section 3.3).  Actions use the variational
 // estimate S = 2 Re(b^dag X) - X^dag A X of b^dag A^-1 b, whose error is
 // quadratic in the solver residual.
 //
@@ -19,6 +21,7 @@
 //               dS = s sum_k Re(L_k^dag dK R_k), L_k = prod_{j<k} (K - r_j^*) v,
 //               R_k = prod_{j>k} (K - r_j) v
 //   FILTERED    minus the POLY force of Q(x) = x P(x) at v = X
+//   RATIO       the POLY force with Q's roots and scale
 // where A~ = (A, D^dag_oe A) and B~ = (B, D_oe B) extend even fields to the
 // full lattice.  Only X and Y are kept per PLAIN/HASENBUSCH term; for
 // polynomial terms the vectors R_k are recomputed segment by segment from
@@ -33,11 +36,10 @@ namespace wd {
 
 static int check_term(const wd_term* t) {
   if (t == nullptr) return fail(WD_ERR_ARG, "term is null");
-  if (t->kind < WD_TERM_PLAIN || t->kind > WD_TERM_FILTERED) return fail(WD_ERR_ARG, "unknown term kind");
-  if (t->kind >= WD_TERM_POLY) {
-    PolyCoef pc;
-    WD_TRY(poly_coef(t->poly, &pc));
-  }
+  if (t->kind < WD_TERM_PLAIN || t->kind > WD_TERM_RATIO) return fail(WD_ERR_ARG, "unknown term kind");
+  PolyCoef pc;
+  if (t->kind == WD_TERM_POLY || t->kind == WD_TERM_FILTERED) WD_TRY(poly_coef(t->poly, &pc));
+  if (t->kind == WD_TERM_RATIO) WD_TRY(ratio_coef(t->poly, t->poly_lo, &pc));
   return WD_OK;
 }
 
@@ -167,6 +169,17 @@ static int poly_apply_hp(wd_ctx* c, double kappa, const wd_poly& P, const Field&
   return convert(c, b, out);
 }
 
+static int roots_apply_hp(wd_ctx* c, double kappa, const PolyCoef& q, const Field& in, const Field& out) {
+  if (!(c->resid_dd && c->gauge_dd)) return roots_apply_f(c, kappa, q, in, out);
+  WsGuard w(c);
+  Field a, b;
+  WD_TRY(w.get(WD_DD, &a));
+  WD_TRY(w.get(WD_DD, &b));
+  WD_TRY(convert(c, in, a));
+  WD_TRY(roots_apply_f(c, kappa, q, a, b));
+  return convert(c, b, out);
+}
+
 static int khat_hp(wd_ctx* c, double kappa, const Field& in, const Field& out) {
   if (!(c->resid_dd && c->gauge_dd)) return khat_any(c, kappa, in, out);
   WsGuard w(c);
@@ -204,6 +217,14 @@ int term_action(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_param
     }
     case WD_TERM_POLY: {
       WD_TRY(poly_apply_hp(c, t.kappa, t.poly, phi, AX));
+      WD_TRY(dot(c, phi, AX, &re, nullptr));
+      *S = re;
+      return WD_OK;
+    }
+    case WD_TERM_RATIO: {
+      PolyCoef q;
+      WD_TRY(ratio_coef(t.poly, t.poly_lo, &q));
+      WD_TRY(roots_apply_hp(c, t.kappa, q, phi, AX));
       WD_TRY(dot(c, phi, AX, &re, nullptr));
       *S = re;
       return WD_OK;
@@ -249,12 +270,20 @@ int term_heatbath(wd_ctx* c, const wd_term& t, const Field& chi, const wd_cg_par
       WD_TRY(mhat(c, t.kappa, true, chi, y));
       return apply_cdag(c, t.kappa, pc, y, phi);
     }
+    case WD_TERM_RATIO: {
+      PolyCoef q;
+      WD_TRY(ratio_coef(t.poly, t.poly_lo, &q));
+      WD_TRY(apply_cdag(c, t.kappa, q, chi, y));    // D^dag chi
+      WD_TRY(zero(c, phi));
+      wd_cg_info info;
+      return cg_solve_ratio(c, t.kappa, q, y, phi, p, &info);
+    }
   }
   return fail(WD_ERR_ARG, "unknown term kind");
 }
 
 // Force from a given solution X (and Y = M_hat X, or nullptr to form it):
-// no solve.  POLY ignores X and Y.  f = FP64 or FP32 arithmetic.
+// no solve.  POLY and RATIO ignore X and Y.  f = FP64 or FP32 arithmetic.
 int term_force_xy(wd_ctx* c, const wd_term& t, const Field& phi, const Field* X, const Field* Y, int f,
                   double coef, double* F) {
   WsGuard w(c);
@@ -281,6 +310,13 @@ int term_force_xy(wd_ctx* c, const wd_term& t, const Field& phi, const Field* X,
       WD_TRY(w.get(f, &phif));
       WD_TRY(convert(c, phi, phif));
       return poly_force(c, t.kappa, pc.zr, pc.zi, pc.scale, phif, coef, F);
+    }
+    case WD_TERM_RATIO: {
+      PolyCoef q;
+      WD_TRY(ratio_coef(t.poly, t.poly_lo, &q));
+      WD_TRY(w.get(f, &phif));
+      WD_TRY(convert(c, phi, phif));
+      return poly_force(c, t.kappa, q.zr, q.zi, q.scale, phif, coef, F);
     }
     case WD_TERM_FILTERED: {
       PolyCoef pc;
@@ -310,6 +346,7 @@ int term_force(wd_ctx* c, const wd_term& t, const Field& phi, const wd_cg_params
       WD_TRY(solve(c, t.kappa, nullptr, b, X, p));
       return term_force_xy(c, t, phi, &X, nullptr, f, coef, F);
     case WD_TERM_POLY:
+    case WD_TERM_RATIO:
       return term_force_xy(c, t, phi, nullptr, nullptr, f, coef, F);
     case WD_TERM_FILTERED:
       WD_TRY(solve(c, t.kappa, &t.poly, phi, X, p));
@@ -494,7 +531,7 @@ int fermion_force_xy(wd_ctx* c, const wd_term* term, const double* phi, const do
   if (!c || !phi || !F) return fail(WD_ERR_ARG, "null argument");
   WD_TRY(check_term(term));
   if (prec != WD_F64 && prec != WD_F32) return fail(WD_ERR_ARG, "fermion_force_xy: prec must be FP64 or FP32");
-  if (term->kind != WD_TERM_POLY && !X) return fail(WD_ERR_ARG, "fermion_force_xy: X is required for this term");
+  if (term->kind != WD_TERM_POLY && term->kind != WD_TERM_RATIO && !X) return fail(WD_ERR_ARG, "fermion_force_xy: X is required for this term");
   if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
   Field fx = wrap_f64(c, X), fy = wrap_f64(c, Y);
   const bool useY = Y != nullptr && (term->kind == WD_TERM_PLAIN || term->kind == WD_TERM_HASENBUSCH);

@@ -563,6 +563,13 @@ struct PolyCoef {
   double s1;                       // s_1 = 1/mu
 };
 int poly_coef(const wd_poly& P, PolyCoef* out);
+// Q = P_hi / P_lo in factored form (no recurrence coefficients)
+int ratio_coef(const wd_poly& hi, const wd_poly& lo, PolyCoef* out);
+// out = Q(K_hat) in from the roots of Q, conjugate pairs as real quadratics;
+// in and out of one format (FP64, FP32 or double-float) and distinct
+int roots_apply_f(wd_ctx* c, double kappa, const PolyCoef& q, const Field& in, const Field& out);
+int cg_solve_ratio(wd_ctx* c, double kappa, const PolyCoef& q, const Field& b, const Field& x,
+                   const wd_cg_params& p, wd_cg_info* info);
 
 // launch helpers
 inline int nblocks(long n, int threads) { return (int)((n + threads - 1) / threads); }

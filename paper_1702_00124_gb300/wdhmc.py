@@ -19,7 +19,7 @@ lib = C.CDLL(_LIB_PATH)
 
 F64, F32, F16, BF16, DF = 0, 1, 2, 3, 4   # DF: double-float (operator calls only)
 RECON_18, RECON_12 = 0, 1
-PLAIN, HASENBUSCH, POLY, FILTERED = 0, 1, 2, 3
+PLAIN, HASENBUSCH, POLY, FILTERED, RATIO = 0, 1, 2, 3, 4
 ERRORS = {1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_NOCONV", 4: "WD_ERR_NAN", 5: "WD_ERR_STATE"}
 
 
@@ -34,7 +34,8 @@ class wd_poly(C.Structure):
 
 
 class wd_term(C.Structure):
-    _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("kappa_h", C.c_double), ("poly", wd_poly)]
+    _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("kappa_h", C.c_double), ("poly", wd_poly),
+                ("poly_lo", wd_poly)]
 
 
 class wd_cg_params(C.Structure):
@@ -147,9 +148,10 @@ def cg_params(tol=1e-10, maxiter=10000, prec=F64, delta=0.0, check_every=0):
     return wd_cg_params(tol, maxiter, prec, delta, check_every)
 
 
-def term(kind, kappa, kappa_h=0.0, poly=None):
-    p = wd_poly(0, 0.0, 0.0) if poly is None else wd_poly(int(poly[0]), float(poly[1]), float(poly[2]))
-    return wd_term(kind, kappa, kappa_h, p)
+def term(kind, kappa, kappa_h=0.0, poly=None, poly_lo=None):
+    def mk(q):
+        return wd_poly(0, 0.0, 0.0) if q is None else wd_poly(int(q[0]), float(q[1]), float(q[2]))
+    return wd_term(kind, kappa, kappa_h, mk(poly), mk(poly_lo))
 
 
 def _ops_array(ops):

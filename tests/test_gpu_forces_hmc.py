@@ -16,18 +16,23 @@ from paper_1702_00124_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 POLY = (4, 0.05, 5.0)
+RATIO_HI, RATIO_LO = (8, 0.05, 5.0), (2, 0.05, 5.0)     # Q = P_8 / P_2 (Section 3.3)
 KAPPA, KAPPA_H = 0.125, 0.115
 
 
 def _oracle_term(kind):
+    from oracle.poly import RatioFilter
     pf = ChebyshevFilter(*POLY)
+    q = RatioFilter(ChebyshevFilter(*RATIO_HI), ChebyshevFilter(*RATIO_LO))
     return {0: actions.term("plain", KAPPA), 1: actions.term("hasenbusch", KAPPA, KAPPA_H),
-            2: actions.term("poly", KAPPA_H, poly=pf), 3: actions.term("filtered", KAPPA_H, poly=pf)}[kind]
+            2: actions.term("poly", KAPPA_H, poly=pf), 3: actions.term("filtered", KAPPA_H, poly=pf),
+            4: actions.term("ratio", KAPPA_H, poly=q)}[kind]
 
 
 def _gpu_term(wd, kind):
     return {0: wd.term(wd.PLAIN, KAPPA), 1: wd.term(wd.HASENBUSCH, KAPPA, KAPPA_H),
-            2: wd.term(wd.POLY, KAPPA_H, poly=POLY), 3: wd.term(wd.FILTERED, KAPPA_H, poly=POLY)}[kind]
+            2: wd.term(wd.POLY, KAPPA_H, poly=POLY), 3: wd.term(wd.FILTERED, KAPPA_H, poly=POLY),
+            4: wd.term(wd.RATIO, KAPPA_H, poly=RATIO_HI, poly_lo=RATIO_LO)}[kind]
 
 
 @pytest.fixture(scope="module", params=[(4, 4, 4, 4), (6, 4, 6, 10)], ids=["4x4x4x4", "6x4x6x10"])
@@ -43,7 +48,7 @@ def setup(request):
     lat.close()
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["plain", "hasenbusch", "poly", "filtered"])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4], ids=["plain", "hasenbusch", "poly", "filtered", "ratio"])
 def test_heatbath_and_action(setup, kind):
     s = setup
     lat, gu, wd = s["lat"], s["gu"], s["wd"]
@@ -61,7 +66,7 @@ def test_heatbath_and_action(setup, kind):
     assert abs(S_ref - chi2) < 1e-9 * chi2
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["plain", "hasenbusch", "poly", "filtered"])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4], ids=["plain", "hasenbusch", "poly", "filtered", "ratio"])
 def test_fermion_force(setup, kind):
     s = setup
     lat, gu, wd = s["lat"], s["gu"], s["wd"]
@@ -81,6 +86,28 @@ def test_fermion_force(setup, kind):
     lat.fermion_force(t_g, phi_e, p, -1.0, F)
     lat.fermion_force(t_g, phi_e, p, 2.0, F)
     assert np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) < 1e-9 * np.linalg.norm(F_ref)
+
+
+def test_ratio_degenerate_and_invalid(setup):
+    """Q = P / P = 1: S = phi^dag phi, phi = chi, zero force.  Filters whose orders
+    do not nest ((n_lo + 1) not dividing (n + 1)) or whose intervals differ are
+    rejected before any work."""
+    s = setup
+    lat, gu, wd = s["lat"], s["gu"], s["wd"]
+    chi_e = gu.pack(lat, s["chi"], 0)
+    t1 = wd.term(wd.RATIO, KAPPA_H, poly=RATIO_HI, poly_lo=RATIO_HI)
+    p = wd.cg_params(tol=1e-12)
+    phi = lat.half_spinor()
+    lat.pf_heatbath(t1, chi_e, p, phi)
+    assert gu.rel_norm_err(gu.unpack(lat, phi, 0), s["chi"]) < 1e-15
+    chi2 = float(np.vdot(s["chi"], s["chi"]).real)
+    assert abs(lat.pf_action(t1, phi, p) - chi2) < 1e-13 * chi2
+    F = lat.algebra_field()
+    lat.fermion_force(t1, phi, p, 1.0, F)
+    assert float(F.abs().max()) == 0.0
+    for hi, lo in ((RATIO_HI, (4, 0.05, 5.0)), (RATIO_HI, (2, 0.05, 6.0)), (RATIO_LO, RATIO_HI)):
+        with pytest.raises(wd.WdError):
+            lat.pf_action(wd.term(wd.RATIO, KAPPA_H, poly=hi, poly_lo=lo), phi, p)
 
 
 def test_gauge_action_and_force(setup):
@@ -240,4 +267,59 @@ def test_trajectory_matches_oracle():
     else:
         assert np.array_equal(gu.host_c(Ub, U0.shape), U0)
     assert r["n_mat"] > 0
+    lat.close()
+
+
+def test_two_filter_trajectory_matches_oracle():
+    """2PF-1MP (Section 3.3, Section 4.2): P_1, Q = P_2 / P_1, the filtered P_2 term and
+    a Hasenbusch term, on four integrator levels, every step in FP64; dH and the final
+    links against the oracle's trajectory from the same draws."""
+    from oracle.poly import RatioFilter
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 4)
+    U0 = synthetic.gauge_field(dims, 0.3, 911)
+    k, kh, beta, tau = 0.124, 0.115, 5.6, 0.4
+    seed, traj = 77, 3
+    p1, p2 = (2, 0.02, 6.0), (8, 0.02, 6.0)
+    f1, f2 = ChebyshevFilter(*p1), ChebyshevFilter(*p2)
+    terms_o = [actions.term("poly", kh, poly=f1), actions.term("ratio", kh, poly=RatioFilter(f2, f1)),
+               actions.term("filtered", kh, poly=f2), actions.term("hasenbusch", k, kh)]
+    terms_g = [wd.term(wd.POLY, kh, poly=p1), wd.term(wd.RATIO, kh, poly=p2, poly_lo=p1),
+               wd.term(wd.FILTERED, kh, poly=p2), wd.term(wd.HASENBUSCH, k, kh)]
+    groups = [2, 1, 0, 0]
+    levels = [(0, 2), (1, 1), (2, 1), (-1, 2)]
+    V = int(np.prod(dims))
+    base = traj * 64
+    P0 = philox.gaussian_field(V * 32, seed, base).reshape(lattice.shape(dims) + (4, 8))
+    phis = []
+    for i, t in enumerate(terms_o):
+        g = philox.gaussian_field(V * 24, seed, base + 1 + i)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        phis.append(actions.heatbath(U0, t, chi))
+
+    def H(U, P):
+        return hmc.kinetic(P) + force.gauge_action(U, beta) + sum(
+            actions.action(U, t, ph)[0] for t, ph in zip(terms_o, phis))
+
+    def fog(grp, U):
+        if grp == -1:
+            return force.gauge_force(U, beta)
+        return sum(force.fermion_force(U, t, ph) for t, ph, g in zip(terms_o, phis, groups) if g == grp)
+
+    U1, P1 = hmc.integrate(U0, P0, hmc.nested(levels, tau, "omelyan"), fog)
+    dH_ref = H(U1, P1) - H(U0, P0)
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U0))
+    ops = wd.wd_schedule_nested(1, tau, [g for g, _ in levels], [n for _, n in levels])
+    p64 = wd.cg_params(tol=1e-14, maxiter=20000)
+    r = lat.hmc_trajectory(terms_g, groups, beta, ops, p64, p64, wd.F64, seed, traj, 0.0)
+    assert abs(r["dH"] - dH_ref) < 1e-9, (r["dH"], dH_ref)
+    import torch
+    Ub = torch.zeros(2 * U0.size, dtype=torch.float64, device="cuda")
+    lat.wd_gauge_store(Ub)
+    if r["accepted"]:
+        assert np.max(np.abs(gu.host_c(Ub, U0.shape) - U1)) < 1e-10
+    else:
+        assert np.array_equal(gu.host_c(Ub, U0.shape), U0)
     lat.close()

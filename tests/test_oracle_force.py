@@ -3,8 +3,8 @@
   * Heat bath: S(phi(chi)) = chi^dag chi for every term kind (the action and
     the heat bath are computed by different routes).
   * Determinant identities of mass preconditioning and polynomial filtering
-    (Section 2, Section 4.1): the Gaussian integrals of the PF-MP terms
-    multiply to det K_hat, checked densely on 2^4.
+    (Section 2, Sections 3.3 and 4.1-4.2): the Gaussian integrals of the PF-MP,
+    2PF, 2MP and 1PF-2MP terms multiply to det K_hat, checked densely on 2^4.
   * Gauge invariance of every action term under random SU(3) transforms.
   * Forces: central finite differences of the actions in extended precision
     (long double, solves to 1e-18), step 1e-5, on links that include the
@@ -109,6 +109,40 @@ def test_2pf_determinant_identity():
     lhs = -(logdet(P1) + logdet(Q) - logdet(P2K))
     assert abs(lhs - logdet(K)) < 1e-9 * abs(logdet(K))
     assert np.allclose(P1 @ Q, D(lambda v: p2.apply(Kop, v)), atol=1e-9 * np.abs(P1 @ Q).max())
+
+
+@pytest.mark.parametrize("with_filter", [False, True], ids=["2MP", "1PF-2MP"])
+def test_two_mass_determinant_identity(with_filter):
+    """2MP (Section 3.3) and 1PF-2MP (Section 4.2) with kappa_1 < kappa_2 < kappa:
+    J_1^-1 (or P(J_1) and [P(J_1) J_1]^-1), M_1 J_2^-1 M_1^dag and M_2 K^-1 M_2^dag,
+    the Hermitian reading of "J_1 J_2^-1" and "J_2 K^-1"; their Gaussian integrals
+    multiply to det K_hat."""
+    dims = (2, 2, 2, 2)
+    U = synthetic.gauge_field(dims, 0.6, 53)
+    k, k2, k1 = 0.125, 0.115, 0.10
+    pf = ChebyshevFilter(4, 0.02, 6.0)
+    shp = lattice.shape(dims) + (4, 3)
+    sup = np.broadcast_to((lattice.parity(dims) == 0)[..., None, None], shp)
+    D = lambda op: dense_matrix(op, sup)[0]
+    K = D(lambda v: wilson.apply_Khat(U, v, k))
+    J1 = D(lambda v: wilson.apply_Khat(U, v, k1))
+    J2 = D(lambda v: wilson.apply_Khat(U, v, k2))
+    M1 = D(lambda v: wilson.apply_Mhat(U, v, k1))
+    M2 = D(lambda v: wilson.apply_Mhat(U, v, k2))
+    if with_filter:
+        PJ = D(lambda v: pf.apply(lambda w: wilson.apply_Khat(U, w, k1), v))
+        first = [PJ, np.linalg.inv(PJ @ J1)]
+    else:
+        first = [np.linalg.inv(J1)]
+    forms = first + [M1 @ np.linalg.inv(J2) @ M1.conj().T, M2 @ np.linalg.inv(K) @ M2.conj().T]
+    logdet = lambda A: np.linalg.slogdet(A)[1]
+    lhs = -sum(logdet(A) for A in forms)
+    assert abs(lhs - logdet(K)) < 1e-9 * abs(logdet(K))
+    # the oracle's hasenbusch term evaluates the same quadratic form
+    phi = lattice.mask(synthetic.spinor_field(dims, 54), dims, 0)
+    v = phi.reshape(-1)[dense_matrix(lambda x: x, sup)[1]]
+    S, _ = actions.action(U, actions.term("hasenbusch", k2, k1), phi, tol=1e-14)
+    assert abs(S - np.vdot(v, forms[-2] @ v).real) < 1e-10 * abs(S)
 
 
 def _fd_check(U, action_of_U, F, links, h=1e-5, rtol=1e-9):
