@@ -407,6 +407,7 @@ def main():
                 info = lat.cg_solve(w["kappa_h"], b, x, wd.cg_params(tol=1e-10, prec=prec), filt=w["poly"])
                 torch.cuda.synchronize()
                 extras[f"filtered_cg_{name}"] = {"s": time.perf_counter() - t, "iters": info["iters"],
+                                                 "reliable_updates": info["reliable_updates"],
                                                  "true_rel_resid": info["true_rel_resid"]}
         lat.wd_set_residual(RESIDUAL_MODE)
         # stand-alone K_hat bandwidth per precision (10 applications each)

@@ -232,6 +232,19 @@ int gaussian_draw(wd_ctx* ctx, int what, int parity, uint64_t seed, uint64_t str
 /* Accept iff u < exp(-dH); host-only, no device work. */
 int metropolis(double dH, double u, int* accept);
 
+/* Cost of an action over n trajectories (Section 3.1, the cost metric):
+ * C = <N_mat> / P_acc, N_mat the K_hat multiplications of one trajectory
+ * (wd_hmc_result.n_mat) and P_acc the Metropolis acceptance rate.  Inputs are
+ * host arrays of length n >= 1: n_mat[i] >= 0, accepted[i] in {0, 1}, dH[i]
+ * not NaN.  Also returned: p_acc_est = <min(1, exp(-dH))>, an estimator of
+ * P_acc with less variance, and <exp(-dH)> with its standard error, which is
+ * 1 at equilibrium for a reversible, area-preserving integrator.  C is +inf
+ * when no trajectory was accepted.  Host-only; needs no context and no GPU. */
+typedef struct {
+  double C, p_acc, p_acc_est, mean_nmat, exp_mdH, exp_mdH_err;
+} wd_cost_result;
+int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n, wd_cost_result* out);
+
 /* ---- HMC trajectory ---------------------------------------------------------- */
 
 /* One operation of an integrator: kind 0 = T[eps]; kind 1 = S[eps] for the

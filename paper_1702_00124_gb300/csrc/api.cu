@@ -381,4 +381,34 @@ int metropolis(double dH, double u, int* accept) {
   return WD_OK;
 }
 
+int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n, wd_cost_result* out) {
+  CHECK_PTR(n_mat);
+  CHECK_PTR(accepted);
+  CHECK_PTR(dH);
+  CHECK_PTR(out);
+  if (n < 1) return fail(WD_ERR_ARG, "wd_cost: n must be >= 1");
+  double sn = 0, sa = 0, se = 0, sx = 0, sx2 = 0;
+  for (int i = 0; i < n; ++i) {
+    if (n_mat[i] < 0) return fail(WD_ERR_ARG, "wd_cost: n_mat must be >= 0");
+    if (accepted[i] != 0 && accepted[i] != 1) return fail(WD_ERR_ARG, "wd_cost: accepted must be 0 or 1");
+    if (std::isnan(dH[i])) return fail(WD_ERR_NAN, "wd_cost: dH is NaN");
+    const double x = std::exp(-dH[i]);
+    sn += (double)n_mat[i];
+    sa += accepted[i];
+    se += x < 1.0 ? x : 1.0;
+    sx += x;
+    sx2 += x * x;
+  }
+  wd_cost_result r;
+  r.mean_nmat = sn / n;
+  r.p_acc = sa / n;
+  r.p_acc_est = se / n;
+  r.C = r.p_acc > 0 ? r.mean_nmat / r.p_acc : INFINITY;
+  r.exp_mdH = sx / n;
+  const double var = n > 1 ? (sx2 - sx * sx / n) / (n - 1) : 0.0;
+  r.exp_mdH_err = n > 1 ? std::sqrt((var > 0 ? var : 0.0) / n) : 0.0;
+  *out = r;
+  return WD_OK;
+}
+
 }  // extern "C"

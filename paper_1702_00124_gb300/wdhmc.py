@@ -59,6 +59,11 @@ class wd_hmc_params(C.Structure):
                 ("seed", C.c_uint64), ("traj_index", C.c_uint64)]
 
 
+class wd_cost_result(C.Structure):
+    _fields_ = [("C", C.c_double), ("p_acc", C.c_double), ("p_acc_est", C.c_double), ("mean_nmat", C.c_double),
+                ("exp_mdH", C.c_double), ("exp_mdH_err", C.c_double)]
+
+
 class wd_hmc_result(C.Structure):
     _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("dH", C.c_double), ("S_gauge0", C.c_double),
                 ("S_gauge1", C.c_double), ("accepted", C.c_int), ("n_mat", C.c_longlong),
@@ -97,6 +102,7 @@ _SIG = {
     "kinetic_energy": ([_P, _P, C.POINTER(_D)], _I),
     "gaussian_draw": ([_P, _I, _I, C.c_uint64, C.c_uint64, _P], _I),
     "metropolis": ([_D, _D, C.POINTER(_I)], _I),
+    "wd_cost": ([C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_D), _I, C.POINTER(wd_cost_result)], _I),
     "hmc_trajectory": ([_P, C.POINTER(wd_hmc_params), _D, C.POINTER(wd_hmc_result)], _I),
     "wd_schedule_nested": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I, C.POINTER(_I)], _I),
     "wd_schedule_generalised": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I,
@@ -185,6 +191,18 @@ def metropolis(dH, u):
     a = C.c_int(0)
     _check(lib.metropolis(dH, u, C.byref(a)))
     return bool(a.value)
+
+
+def wd_cost(n_mat, accepted, dH):
+    """C = <N_mat> / P_acc over trajectories (host arrays; see the C header)."""
+    n = len(n_mat)
+    if len(accepted) != n or len(dH) != n:
+        raise ValueError("n_mat, accepted and dH must have one entry per trajectory")
+    r = wd_cost_result()
+    _check(lib.wd_cost((C.c_longlong * max(n, 1))(*[int(v) for v in n_mat]),
+                       (C.c_int * max(n, 1))(*[int(v) for v in accepted]),
+                       (C.c_double * max(n, 1))(*[float(v) for v in dH]), n, C.byref(r)))
+    return {k: getattr(r, k) for k, _ in wd_cost_result._fields_}
 
 
 class Batch:

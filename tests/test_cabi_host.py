@@ -96,6 +96,28 @@ def test_metropolis_host(wd):
         wd.metropolis(0.1, 1.5)
 
 
+def test_cost_matches_oracle(wd):
+    """wd_cost (C = N_mat / P_acc, Section 3.1) against the oracle's definition on
+    seeded trajectory records, and its argument checks."""
+    import math
+    from oracle.cost import cost
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 37, 500):
+        nm = rng.integers(1000, 50000, n)
+        dH = rng.normal(0.3, 0.8, n)
+        acc = (rng.random(n) < np.minimum(1, np.exp(-dH))).astype(int)
+        got, want = wd.wd_cost(nm, acc, dH), cost(nm, acc, dH)
+        for k, v in want.items():
+            if math.isinf(v):
+                assert math.isinf(got[k]), k
+            else:
+                assert abs(got[k] - v) <= 1e-12 * max(1.0, abs(v)), (n, k, got[k], v)
+    assert math.isinf(wd.wd_cost([10, 20], [0, 0], [5.0, 6.0])["C"])
+    for bad in (([1], [2], [0.0]), ([-1], [1], [0.0]), ([1], [1], [float("nan")]), ([], [], [])):
+        with pytest.raises(wd.WdError):
+            wd.wd_cost(*bad)
+
+
 def test_schedule_argument_errors(wd):
     with pytest.raises(wd.WdError) as e:
         wd.wd_schedule_nested(3, 1.0, [0], [1])
