@@ -24,20 +24,48 @@ namespace wd {
 
 constexpr int H_THREADS = 128;
 
+// cos x and sin(x)/x from y = -x^2 by their Taylor series through x^14; for
+// |x| <= 0.5 the first omitted terms are below 1e-18.
+__device__ __forceinline__ double cos_series(double y) {
+  double t = 1.0 / 87178291200.0;              // 1/14!
+  t = fma(t, y, 1.0 / 479001600.0);            // 1/12!
+  t = fma(t, y, 1.0 / 3628800.0);
+  t = fma(t, y, 1.0 / 40320.0);
+  t = fma(t, y, 1.0 / 720.0);
+  t = fma(t, y, 1.0 / 24.0);
+  t = fma(t, y, 0.5);
+  return fma(t, y, 1.0);
+}
+__device__ __forceinline__ double sinc_series(double y) {
+  double t = 1.0 / 1307674368000.0;            // 1/15!
+  t = fma(t, y, 1.0 / 6227020800.0);           // 1/13!
+  t = fma(t, y, 1.0 / 39916800.0);
+  t = fma(t, y, 1.0 / 362880.0);
+  t = fma(t, y, 1.0 / 5040.0);
+  t = fma(t, y, 1.0 / 120.0);
+  t = fma(t, y, 1.0 / 6.0);
+  return fma(t, y, 1.0);
+}
+
+// Q is Hermitian and traceless: Q2 = Q^2 is Hermitian, so its diagonal is
+// real and its lower triangle the conjugate of the upper one.
 __device__ __forceinline__ void cayley_hamilton_exp(const cpx<double> (&Q)[9], cpx<double> (&E)[9]) {
+  const double q00 = Q[0].r, q11 = Q[4].r, q22 = Q[8].r;
+  const cpx<double> q01 = Q[1], q02 = Q[2], q12 = Q[5];
+  const double n01 = norm2(q01), n02 = norm2(q02), n12 = norm2(q12);
   cpx<double> Q2[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Q2[3 * i + j] = Q[3 * i] * Q[j] + Q[3 * i + 1] * Q[3 + j] + Q[3 * i + 2] * Q[6 + j];
+  Q2[0] = mk(q00 * q00 + n01 + n02, 0.0);
+  Q2[4] = mk(q11 * q11 + n01 + n12, 0.0);
+  Q2[8] = mk(q22 * q22 + n02 + n12, 0.0);
+  Q2[1] = (q00 + q11) * q01 + q02 * conj(q12);
+  Q2[2] = (q00 + q22) * q02 + q01 * q12;
+  Q2[5] = (q11 + q22) * q12 + conj(q01) * q02;
+  Q2[3] = conj(Q2[1]);
+  Q2[6] = conj(Q2[2]);
+  Q2[7] = conj(Q2[5]);
   const double c1 = 0.5 * (Q2[0].r + Q2[4].r + Q2[8].r);
-  // c0 = det Q = tr(Q^3) / 3
-  double c0 = 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) c0 += (Q2[3 * i + k] * Q[3 * k + i]).r;
-  c0 /= 3.0;
+  // c0 = det Q = q00 q11 q22 + 2 Re(q01 q12 q02^*) - q00 |q12|^2 - q11 |q02|^2 - q22 |q01|^2
+  const double c0 = q00 * q11 * q22 + 2.0 * (q01 * q12 * conj(q02)).r - q00 * n12 - q11 * n02 - q22 * n01;
   cpx<double> f0, f1, f2;
   if (c1 < 1e-24) {
     f0 = mk(1.0, 0.0);
@@ -51,16 +79,31 @@ __device__ __forceinline__ void cayley_hamilton_exp(const cpx<double> (&Q)[9], c
     const double c0max = 2.0 * t3 * st3;           // 2 (c1/3)^{3/2}
     double r = c0a / c0max;
     r = r > 1.0 ? 1.0 : r;
-    const double th = acos(r);
-    double s3, c3;
-    sincos(th / 3.0, &s3, &c3);
-    const double u = st3 * c3;
-    const double w = 1.7320508075688772935 * st3 * s3;   // sqrt(c1) sin(th/3)
-    const double u2 = u * u, w2 = w * w;
-    double sw, cw, su, cu;
-    sincos(w, &sw, &cw);
-    sincos(u, &su, &cu);
-    const double xi0 = fabs(w) < 0.05 ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sw / w;
+    // cs = cos(th/3), th = acos(r) in [0, pi/2]: the root of 4 cs^3 - 3 cs = r
+    // in [cos(pi/6), 1], where the derivative 12 cs^2 - 3 lies in [6, 9]; an
+    // FP32 seed and two Newton steps in FP64
+    double cs = (double)cosf(acosf((float)r) * (1.0f / 3.0f));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) cs -= (cs * (4.0 * cs * cs - 3.0) - r) / (12.0 * cs * cs - 3.0);
+    const double u = st3 * cs;
+    const double u2 = u * u;
+    const double w2 = c1 * (1.0 - cs) * (1.0 + cs);  // w = sqrt(c1) sin(th/3)
+    double cw, xi0, cu, su;
+    if (w2 <= 0.25) {
+      cw = cos_series(-w2);
+      xi0 = sinc_series(-w2);
+    } else {
+      const double w = sqrt(w2);
+      double sw;
+      sincos(w, &sw, &cw);
+      xi0 = sw / w;
+    }
+    if (u2 <= 0.25) {
+      cu = cos_series(-u2);
+      su = u * sinc_series(-u2);
+    } else {
+      sincos(u, &su, &cu);
+    }
     const cpx<double> e2 = mk(cu * cu - su * su, 2.0 * su * cu);   // exp(2iu)
     const cpx<double> em = mk(cu, -su);                              // exp(-iu)
     const cpx<double> h0 = (u2 - w2) * e2 + em * mk(8 * u2 * cw, 2 * u * (3 * u2 + w2) * xi0);

@@ -131,7 +131,7 @@ def test_steps_and_kinetic(setup):
     Pe = gu.alg_to_dev(lat, P)
     assert abs(lat.kinetic_energy(Pe) - hmc.kinetic(P)) < 1e-12 * hmc.kinetic(P)
     import torch
-    for eps in (0.3, 0.01, 1e-4):
+    for eps in (2.0, 0.3, 0.01, 1e-4):     # 2.0: angles above the series range
         lat.wd_gauge_load(gu.dev(s["U"]))
         lat.step_T(Pe, eps)
         Ub = torch.zeros(2 * s["U"].size, dtype=torch.float64, device="cuda")
