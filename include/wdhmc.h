@@ -279,6 +279,10 @@ typedef struct {
 } wd_hmc_result;
 
 /* Heat bath, momentum draw, integration, accept/reject with uniform u (host).
+ * Draws: momenta P_a ~ N(0,1) per coordinate (density exp(-sum tr P^2)) from
+ * Philox stream 64 traj_index; the noise of term i is chi ~ exp(-chi^dag chi)
+ * (Section 2: real and imaginary parts N(0, 1/2)), the stream 64 traj_index
+ * + 1 + i draw of gaussian_draw scaled by 1/sqrt(2).
  * On rejection the context's gauge field is restored. */
 int hmc_trajectory(wd_ctx* ctx, const wd_hmc_params* p, double u, wd_hmc_result* res);
 

@@ -123,9 +123,10 @@ def main(argv=None):
     ap.add_argument("--poly", type=float, nargs=3, default=[8, 0.005, 8.0], help="n eps lam of P (P_1)")
     ap.add_argument("--poly2", type=float, nargs=3, default=[26, 0.005, 8.0], help="n eps lam of P_2")
     ap.add_argument("--actions", nargs="+", default=["1PF", "1MP", "PF-MP"])
-    ap.add_argument("--scales", type=int, nargs="+", default=[3, 4, 6, 8],
+    ap.add_argument("--scales", type=int, nargs="+", default=[6, 8, 12, 16],
                     help="outermost step counts of the grid; inner terms take 2x, the gauge 4x")
-    ap.add_argument("--therm-gauge", type=int, default=300, help="pure-gauge thermalisation trajectories")
+    ap.add_argument("--therm-gauge", type=int, default=200, help="pure-gauge thermalisation trajectories")
+    ap.add_argument("--gauge-steps", type=int, default=40, help="Omelyan steps of a pure-gauge trajectory")
     ap.add_argument("--therm", type=int, default=40, help="thermalisation trajectories with fermions")
     ap.add_argument("--traj", type=int, default=20)
     ap.add_argument("--seed", type=int, default=20170201)
@@ -141,12 +142,17 @@ def main(argv=None):
         return 1.0 - lat.gauge_action(a.beta) / (6 * vol * a.beta)
 
     # pure-gauge trajectories bring the links near the equilibrium plaquette cheaply,
-    # then trajectories with the fermions (PF-MP) finish the thermalisation
-    _, c = run(lat, [], a.beta, wd.wd_schedule_generalised(1, 1.0, [-1], [12]), a.therm_gauge, a.seed)
+    # then trajectories with the fermions (PF-MP, steps twice as fine as the finest
+    # grid point) finish the thermalisation.  Far from equilibrium the forces are
+    # large: too coarse a step there gives |dH| >> 1 and a chain that never moves
+    # (dH > 0) or drifts on integration error (dH < 0).
+    _, c = run(lat, [], a.beta, wd.wd_schedule_generalised(1, 1.0, [-1], [a.gauge_steps]), a.therm_gauge, a.seed)
     print(json.dumps({"thermalisation": "pure gauge", "trajectories": a.therm_gauge, "p_acc": c["p_acc"],
                       "mean_plaquette": plaquette()}), flush=True)
     terms = action("PF-MP", a.kappa, a.kappa_h, poly)
-    recs, c = run(lat, terms, a.beta, schedule([6, 12, 12], 24), a.therm, a.seed + 1, first_traj=a.therm_gauge)
+    n0 = 2 * max(a.scales)
+    recs, c = run(lat, terms, a.beta, schedule([n0, 2 * n0, 2 * n0], 4 * n0), a.therm, a.seed + 1,
+                  first_traj=a.therm_gauge)
     tail = wd.wd_cost([r["n_mat"] for r in recs[-10:]], [r["accepted"] for r in recs[-10:]],
                       [r["dH"] for r in recs[-10:]])
     print(json.dumps({"thermalisation": "PF-MP", "trajectories": a.therm, "p_acc": c["p_acc"],

@@ -652,7 +652,10 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   begin(PH_HB);
   WD_TRY(gaussian_draw_k(c, 1, 0, p->seed, base, c->mom));
   for (int i = 0; i < p->nterms; ++i) {
+    // chi ~ exp(-chi^dag chi) (Section 2): real and imaginary parts N(0, 1/2),
+    // the unit-variance Philox draw scaled by 1/sqrt(2)
     WD_TRY(gaussian_draw_k(c, 0, 0, p->seed, base + 1 + i, (double*)chi.data));
+    WD_TRY(axpby(c, M_SQRT1_2, chi, 0.0, chi, chi));
     WD_TRY(term_heatbath(c, p->terms[i], chi, p->cg_acc, phi[i]));
   }
   end();

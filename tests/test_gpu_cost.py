@@ -63,3 +63,47 @@ def test_sweep_restores_links_and_orders_by_cost(env):
     assert {tuple(r["nsteps"]) for r in rows} == {(2, 4), (4, 8)}
     for r in rows:
         assert 0.0 <= r["p_acc"] <= 1.0 and r["mean_nmat"] > 0
+
+
+def test_heatbath_noise_and_momenta_distributions(env):
+    """Section 2: momenta with density exp(-sum tr P^2) and pseudofermion noise with
+    density exp(-chi^dag chi).  With beta = 0 and one PLAIN term, H_0 = sum tr P^2 +
+    chi^dag chi has mean 16 V (32 V coordinates, P_a ~ N(0, 1)) + 6 V (6 V complex
+    components of variance 1) and standard deviation sqrt(22 V)."""
+    import torch
+    lat0, cost, wd, _ = env
+    dims = (8, 8, 8, 8)
+    V = int(np.prod(dims))
+    lat = wd.Lattice(dims)
+    U = synthetic.gauge_field(dims, 0.3, 99)
+    lat.wd_gauge_load(torch.from_numpy(U.view(np.float64).reshape(-1)).cuda())
+    ops = cost.schedule([1], 1, tau=1e-3)
+    p = wd.cg_params(tol=1e-12, maxiter=20000)
+    H0 = []
+    for i in range(4):
+        r = lat.hmc_trajectory([wd.term(wd.PLAIN, 0.12)], [0], 0.0, ops, p, p, wd.F64, 31, i, 0.5)
+        H0.append(r["H0"])
+    lat.close()
+    assert abs(np.mean(H0) - 22 * V) < 5 * math.sqrt(22 * V / len(H0)), (np.mean(H0) / V, H0)
+
+
+def test_hmc_exactness_identity(env):
+    """<exp(-dH)> = 1 over an equilibrated chain (reversible, area-preserving
+    integrator; momenta and pseudofermions from the conditional distributions of
+    Section 2).  A wrong noise normalisation or an irreversible schedule moves it by
+    orders of magnitude; 4^3 x 8, PLAIN at kappa = 0.14, leapfrog with 8 fermion and
+    32 gauge steps, after pure-gauge thermalisation."""
+    import torch
+    _, cost, wd, _ = env
+    dims = (4, 4, 4, 8)
+    lat = wd.Lattice(dims)
+    U = synthetic.gauge_field(dims, 0.5, 11)
+    lat.wd_gauge_load(torch.from_numpy(U.view(np.float64).reshape(-1)).cuda())
+    cost.run(lat, [], 5.6, wd.wd_schedule_generalised(1, 1.0, [-1], [20]), 200, 1)
+    terms = [wd.term(wd.PLAIN, 0.14)]
+    ops = cost.schedule([8], 32)
+    cost.run(lat, terms, 5.6, ops, 40, 2, first_traj=1000)                 # settle with fermions
+    _, c = cost.run(lat, terms, 5.6, ops, 160, 3, first_traj=2000)
+    lat.close()
+    assert c["p_acc"] > 0.5
+    assert abs(c["exp_mdH"] - 1.0) < 4 * c["exp_mdH_err"] + 0.05, c

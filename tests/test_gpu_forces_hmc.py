@@ -188,7 +188,8 @@ def test_bench_configuration_trajectory():
     phis = []
     for i, t in enumerate(terms_o):
         g = philox.gaussian_field(V * 24, seed, base + 1 + i)
-        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        # chi ~ exp(-chi^dag chi): the unit-variance draw over sqrt(2) (Section 2)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0) / np.sqrt(2)
         phis.append(actions.heatbath(U0, t, chi))
 
     def H(U, P):
@@ -239,7 +240,8 @@ def test_trajectory_matches_oracle():
     phis = []
     for i, t in enumerate(terms_o):
         g = philox.gaussian_field(V * 24, seed, base + 1 + i)
-        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        # chi ~ exp(-chi^dag chi): the unit-variance draw over sqrt(2) (Section 2)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0) / np.sqrt(2)
         phis.append(actions.heatbath(U0, t, chi))
 
     def H(U, P):
@@ -295,7 +297,8 @@ def test_two_filter_trajectory_matches_oracle():
     phis = []
     for i, t in enumerate(terms_o):
         g = philox.gaussian_field(V * 24, seed, base + 1 + i)
-        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0)
+        # chi ~ exp(-chi^dag chi): the unit-variance draw over sqrt(2) (Section 2)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(dims) + (4, 3)), dims, 0) / np.sqrt(2)
         phis.append(actions.heatbath(U0, t, chi))
 
     def H(U, P):
