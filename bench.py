@@ -350,7 +350,7 @@ def main():
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None,
-                "traffic": traffic, "kernel": "k_hop FP32 (all variants), 12-real links",
+                "traffic": traffic, "kernel": "k_hop_st FP32 (all variants, links staged by cp.async), 12-real links",
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
                 "sampled_launches": prof["launches"],
                 "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
