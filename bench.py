@@ -47,12 +47,12 @@ DEFAULT_WORKLOAD = "c5_32x32x32x64"
 LEVELS = [(0, 10), (1, 1), (-1, 2)]
 # Residual recomputation of the mixed-precision solves: 0 = FP64, 1 =
 # double-float (2 x FP32, about 44-48 bits; b, x, r and dots stay FP64).
-# At this volume the double-float hop takes 0.70 ms against 2.08 ms in FP64.
+# At this volume the double-float hop takes 0.50-0.58 ms against 2.08 ms in FP64.
 RESIDUAL_MODE = 1
 # K_hat applications of one trajectory of the default workload, counted by
 # the library's N_mat counter (algorithmic count; the reference arm scales
 # its per-K_hat time by it).
-N_MAT_PER_TRAJ = 19350
+N_MAT_PER_TRAJ = 20305
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hop_f32_c5_32x32x32x64.md")
 
 
