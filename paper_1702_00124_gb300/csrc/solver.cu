@@ -230,10 +230,14 @@ static int true_residual(wd_ctx* c, const Op& op, const Field& b, const Field& x
 
 // Default reliable-update factor per sloppy precision: the iterated residual
 // of FP32 stays faithful over larger reductions than that of 16-bit storage.
-// The polynomial operators are well conditioned and their FP64 application
-// costs n+1 FP64 K_hat, so they recompute the residual less often.
+// The Chebyshev-recurrence operators (P, K P) are well conditioned, accurate
+// to a few u_FP32 in FP32, and their FP64 application costs n+1 FP64 K_hat, so
+// they recompute the residual less often.  The root product Q = P_2 / P_1 is
+// not: each real quadratic factor loses about u / |z|^2 on low modes, up to
+// 6e-5 relative for P_26 / P_8 on [0.005, 8], and a sloppy cycle asked to gain
+// 1e-5 stalls; it takes the K_hat factor.
 static double default_delta(int prec, OpKind kind) {
-  if (kind != OP_K && prec == WD_F32) return 1e-5;
+  if ((kind == OP_KP || kind == OP_P) && prec == WD_F32) return 1e-5;
   switch (prec) {
     case WD_F32: return 1e-3;
     case WD_F16: return 5e-2;

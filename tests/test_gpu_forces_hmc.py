@@ -326,3 +326,25 @@ def test_two_filter_trajectory_matches_oracle():
     else:
         assert np.array_equal(gu.host_c(Ub, U0.shape), U0)
     lat.close()
+
+
+def test_ratio_heatbath_wide_filters_mixed_precision():
+    """Q = P_26 / P_8 on [0.005, 8] at kappa = 0.15: the FP32 root product loses up to
+    6e-5 relative on low modes, and the mixed-precision heat bath must still converge
+    (reliable-update factor of the K_hat class) and give S(phi) = chi^dag chi."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 8)
+    U = synthetic.gauge_field(dims, 0.4, 577)
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U))
+    t = wd.term(wd.RATIO, 0.15, poly=(26, 0.005, 8.0), poly_lo=(8, 0.005, 8.0))
+    chi = lat.half_spinor()
+    lat.gaussian_draw(0, 0, 5, 5, chi)
+    phi = lat.half_spinor()
+    lat.pf_heatbath(t, chi, wd.cg_params(tol=1e-10, prec=wd.F32, maxiter=20000), phi)
+    S = lat.pf_action(t, phi, wd.cg_params(tol=1e-12))
+    chi2 = float((chi * chi).sum())
+    assert abs(S - chi2) < 1e-8 * chi2, (S, chi2)
+    lat.close()
