@@ -108,6 +108,20 @@ def test_reversibility(md_setup):
     assert np.max(np.abs(U1 @ su3.dagger(U1) - eye)) < 1e-14
 
 
+@pytest.mark.parametrize("kind", ["leapfrog", "omelyan"])
+def test_generalised_scheme_reversible(md_setup, kind):
+    """Section 3.2's overlay with step counts whose events coincide in time (2 and 4
+    steps): the list of operations is not a palindrome at the ties, but coincident S
+    steps commute, so integrating back with -P returns to the start."""
+    U, P, H, forces = md_setup
+    mk = hmc.leapfrog if kind == "leapfrog" else hmc.omelyan
+    ops = hmc.generalised([mk(2, 0.3, 1), mk(4, 0.3, 0)], 0.3)
+    U1, P1 = hmc.integrate(U, P, ops, forces)
+    U2, P2 = hmc.integrate(U1, -P1, ops, forces)
+    assert np.max(np.abs(U2 - U)) < 1e-10
+    assert np.max(np.abs(-P2 - P)) < 1e-9
+
+
 def test_metropolis():
     assert hmc.metropolis(-0.1, 0.999)
     assert hmc.metropolis(0.5, 0.5)          # exp(-0.5) = 0.607 > 0.5
