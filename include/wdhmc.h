@@ -242,6 +242,7 @@ int metropolis(double dH, double u, int* accept);
  * when no trajectory was accepted.  Host-only; needs no context and no GPU. */
 typedef struct {
   double C, p_acc, p_acc_est, mean_nmat, exp_mdH, exp_mdH_err;
+  double C_est;   /* <N_mat> / p_acc_est, +inf when p_acc_est is 0 */
 } wd_cost_result;
 int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n, wd_cost_result* out);
 
@@ -285,6 +286,39 @@ typedef struct {
  * + 1 + i draw of gaussian_draw scaled by 1/sqrt(2).
  * On rejection the context's gauge field is restored. */
 int hmc_trajectory(wd_ctx* ctx, const wd_hmc_params* p, double u, wd_hmc_result* res);
+
+/* hmc_trajectory on host buffers (Section 2: one trajectory, as above): the
+ * lexicographic FP64 links U_in (HOST, V * 72 doubles) are copied to the
+ * device with one cudaMemcpyAsync and loaded, the trajectory runs, and the
+ * context's links afterwards (the new ones if accepted, else U_in's) are
+ * stored and copied back to U_out (HOST, may be U_in) with one
+ * cudaMemcpyAsync; the call returns after that copy.  Pinned host memory
+ * makes the copies asynchronous DMA.  The device staging buffer (V * 72
+ * doubles) is allocated on the first call and kept by the context. */
+int hmc_trajectory_host(wd_ctx* ctx, const wd_hmc_params* p, double u, const double* U_in, double* U_out,
+                        wd_hmc_result* res);
+
+/* The molecular-dynamics integration alone, on caller-held momenta (Section 2,
+ * eqs. for T-hat and S-hat: T[eps] U = exp(i eps P) U, S[eps] P = P - eps F;
+ * Section 3.2 for the schedule): ops are applied in order to the context's
+ * links and to P (device algebra field); an S op of group g adds -eps F of
+ * every term with term_group g (g = -1: the gauge action, beta > 0) to P.
+ * The pseudofermions phi[i] (host array of nterms device half spinors) are
+ * held fixed.  No heat bath, no Hamiltonian, no Metropolis test, no restore
+ * of the links.  Solves inside forces use cg_md (FP64 when force_prec is
+ * WD_F64).  *n_force_evals (may be NULL) = force evaluations made. */
+typedef struct {
+  int nterms;
+  const wd_term* terms;      /* host array */
+  const int* term_group;     /* host array: integrator group of each term */
+  const double* const* phi;  /* host array of nterms device half spinors */
+  double beta;               /* gauge action coupling; <= 0 disables S_G */
+  int nops;
+  const wd_op* ops;          /* host array: the integrator */
+  wd_cg_params cg_md;
+  int force_prec;            /* WD_F64 or WD_F32 force kernels */
+} wd_integrate_params;
+int integrate(wd_ctx* ctx, double* P, const wd_integrate_params* p, int* n_force_evals);
 
 /* Build integrator schedules on the host (Section 3.2).  kind 0 = leapfrog,
  * 1 = Omelyan 2MN.  nested: levels[i] = steps of group i per enclosing T,

@@ -27,5 +27,6 @@ def cost(n_mat, accepted, dH):
     else:
         err = 0.0
     C = mean_nmat / p_acc if p_acc > 0 else math.inf
+    C_est = mean_nmat / p_acc_est if p_acc_est > 0 else math.inf
     return {"C": C, "p_acc": p_acc, "p_acc_est": p_acc_est, "mean_nmat": mean_nmat,
-            "exp_mdH": exp_mdH, "exp_mdH_err": err}
+            "exp_mdH": exp_mdH, "exp_mdH_err": err, "C_est": C_est}

@@ -87,7 +87,6 @@ def run(lat, terms, beta, ops, n_traj, seed, first_traj=0, cg_md=None, cg_acc=No
         r["n_mat_counter"] = lat.wd_nmat() - n0
         recs.append(r)
     cost = wd.wd_cost([r["n_mat"] for r in recs], [r["accepted"] for r in recs], [r["dH"] for r in recs])
-    cost["C_est"] = cost["mean_nmat"] / cost["p_acc_est"] if cost["p_acc_est"] > 0 else math.inf
     return recs, cost
 
 

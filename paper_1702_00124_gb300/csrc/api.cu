@@ -138,6 +138,7 @@ int wd_context_destroy(wd_ctx* c) {
   cudaFree(c->cgs);
   cudaFree(c->gauge_backup);
   cudaFree(c->mom);
+  cudaFree(c->lex_stage);
   if (c->cgs_host) cudaFreeHost(c->cgs_host);
   if (c->host_scalar) cudaFreeHost(c->host_scalar);
   for (auto& f : c->pool) {
@@ -404,6 +405,7 @@ int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n
   r.p_acc = sa / n;
   r.p_acc_est = se / n;
   r.C = r.p_acc > 0 ? r.mean_nmat / r.p_acc : INFINITY;
+  r.C_est = r.p_acc_est > 0 ? r.mean_nmat / r.p_acc_est : INFINITY;
   r.exp_mdH = sx / n;
   const double var = n > 1 ? (sx2 - sx * sx / n) / (n - 1) : 0.0;
   r.exp_mdH_err = n > 1 ? std::sqrt((var > 0 ? var : 0.0) / n) : 0.0;

@@ -613,10 +613,99 @@ int gaussian_draw(wd_ctx* c, int what, int parity, uint64_t seed, uint64_t strea
   return gaussian_draw_k(c, what, parity, seed, stream, out);
 }
 
+}  // extern "C"
+
+namespace wd {
+
+// Phase timing of a trajectory: (phase, start, stop) events on the context
+// stream, read once at the end.
+struct Phases {
+  struct Mark { int phase; cudaEvent_t e0, e1; };
+  wd_ctx* c;
+  std::vector<Mark> marks;
+  void begin(int phase) {
+    Mark m{phase, nullptr, nullptr};
+    cudaEventCreate(&m.e0);
+    cudaEventCreate(&m.e1);
+    cudaEventRecord(m.e0, c->stream);
+    marks.push_back(m);
+  }
+  void end() { cudaEventRecord(marks.back().e1, c->stream); }
+  ~Phases() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.e0);
+      cudaEventDestroy(m.e1);
+    }
+  }
+};
+enum { PH_HB = 0, PH_H, PH_T, PH_GF, PH_F0 };
+
+// The integrator on momenta P (Section 2: T[eps] U = exp(i eps P) U,
+// S[eps] P = P - eps F; Section 3.2: the schedule), pseudofermions fixed.
+static int run_ops(wd_ctx* c, double* P, int nterms, const wd_term* terms, const int* groups, const Field* phi,
+                   double beta, int nops, const wd_op* ops, const wd_cg_params& md, int fprec, int* nf_out,
+                   Phases* ph) {
+  int nf = 0;
+  for (int k = 0; k < nops; ++k) {
+    const wd_op& o = ops[k];
+    if (o.kind == 0) {
+      if (ph) ph->begin(PH_T);
+      WD_TRY(step_T_k(c, P, o.eps));
+      if (ph) ph->end();
+    } else {
+      if (o.group == -1 && beta > 0) {
+        if (ph) ph->begin(PH_GF);
+        WD_TRY(gauge_force_k(c, beta, fprec, -o.eps, P));
+        if (ph) ph->end();
+        ++nf;
+      }
+      for (int i = 0; i < nterms; ++i) {
+        if (groups[i] != o.group) continue;
+        if (ph) ph->begin(o.group >= 0 && o.group < 4 ? PH_F0 + o.group : PH_GF);
+        WD_TRY(term_force(c, terms[i], phi[i], md, -o.eps, P));
+        if (ph) ph->end();
+        ++nf;
+      }
+    }
+  }
+  if (nf_out) *nf_out = nf;
+  return WD_OK;
+}
+
+static int check_ops(int nops, const wd_op* ops) {
+  if (nops < 1 || !ops) return fail(WD_ERR_ARG, "empty integrator");
+  for (int k = 0; k < nops; ++k)
+    if (ops[k].kind != 0 && ops[k].kind != 1) return fail(WD_ERR_ARG, "op kind must be 0 (T) or 1 (S)");
+  return WD_OK;
+}
+
+}  // namespace wd
+
+extern "C" {
+
+int integrate(wd_ctx* c, double* P, const wd_integrate_params* p, int* n_force_evals) {
+  if (!c || !P || !p) return fail(WD_ERR_ARG, "null argument");
+  if (p->nterms < 0 || (p->nterms > 0 && (!p->terms || !p->term_group || !p->phi))) return fail(WD_ERR_ARG, "bad terms");
+  WD_TRY(check_ops(p->nops, p->ops));
+  for (int i = 0; i < p->nterms; ++i) {
+    WD_TRY(check_term(&p->terms[i]));
+    if (!p->phi[i]) return fail(WD_ERR_ARG, "pseudofermion pointer is null");
+  }
+  WD_TRY(check_cg(&p->cg_md));
+  if (!c->have_gauge) return fail(WD_ERR_STATE, "no gauge field loaded");
+  wd_cg_params md = p->cg_md;
+  md.prec = p->force_prec == WD_F64 ? WD_F64 : p->cg_md.prec;
+  const int fprec = p->force_prec == WD_F64 ? WD_F64 : WD_F32;
+  std::vector<Field> phi(p->nterms);
+  for (int i = 0; i < p->nterms; ++i) phi[i] = wrap_f64(c, p->phi[i]);
+  return run_ops(c, P, p->nterms, p->terms, p->term_group, phi.data(), p->beta, p->nops, p->ops, md, fprec,
+                 n_force_evals, nullptr);
+}
+
 int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* res) {
   if (!c || !p || !res) return fail(WD_ERR_ARG, "null argument");
   if (p->nterms < 0 || (p->nterms > 0 && (!p->terms || !p->term_group))) return fail(WD_ERR_ARG, "bad terms");
-  if (p->nops < 1 || !p->ops) return fail(WD_ERR_ARG, "empty integrator");
+  WD_TRY(check_ops(p->nops, p->ops));
   if (!(u >= 0.0 && u < 1.0)) return fail(WD_ERR_ARG, "u must be in [0, 1)");
   for (int i = 0; i < p->nterms; ++i) WD_TRY(check_term(&p->terms[i]));
   WD_TRY(check_cg(&p->cg_md));
@@ -636,18 +725,9 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   Field chi;
   WD_TRY(w.get(WD_F64, &chi));
   for (auto& f : phi) WD_TRY(w.get(WD_F64, &f));
-  // phase timing: (phase, start, stop) events on the context stream, read at the end
-  enum { PH_HB = 0, PH_H, PH_T, PH_GF, PH_F0 };
-  struct Mark { int phase; cudaEvent_t e0, e1; };
-  std::vector<Mark> marks;
-  auto begin = [&](int phase) {
-    Mark m{phase, nullptr, nullptr};
-    cudaEventCreate(&m.e0);
-    cudaEventCreate(&m.e1);
-    cudaEventRecord(m.e0, c->stream);
-    marks.push_back(m);
-  };
-  auto end = [&]() { cudaEventRecord(marks.back().e1, c->stream); };
+  Phases ph{c, {}};
+  auto begin = [&](int phase) { ph.begin(phase); };
+  auto end = [&]() { ph.end(); };
   // momenta and pseudofermions
   begin(PH_HB);
   WD_TRY(gaussian_draw_k(c, 1, 0, p->seed, base, c->mom));
@@ -681,28 +761,8 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   end();
   int nf = 0;
   const int fprec = p->force_prec == WD_F64 ? WD_F64 : WD_F32;
-  for (int k = 0; k < p->nops; ++k) {
-    const wd_op& o = p->ops[k];
-    if (o.kind == 0) {
-      begin(PH_T);
-      WD_TRY(step_T_k(c, c->mom, o.eps));
-      end();
-    } else {
-      if (o.group == -1 && p->beta > 0) {
-        begin(PH_GF);
-        WD_TRY(gauge_force_k(c, p->beta, fprec, -o.eps, c->mom));
-        end();
-        ++nf;
-      }
-      for (int i = 0; i < p->nterms; ++i) {
-        if (p->term_group[i] != o.group) continue;
-        begin(o.group >= 0 && o.group < 4 ? PH_F0 + o.group : PH_GF);
-        WD_TRY(term_force(c, p->terms[i], phi[i], md, -o.eps, c->mom));
-        end();
-        ++nf;
-      }
-    }
-  }
+  WD_TRY(run_ops(c, c->mom, p->nterms, p->terms, p->term_group, phi.data(), p->beta, p->nops, p->ops, md, fprec,
+                 &nf, &ph));
   begin(PH_H);
   WD_TRY(hamiltonian(&res->H1, &res->S_gauge1));
   end();
@@ -719,17 +779,29 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   res->n_mat = c->nmat - nmat0;
   WD_CUDA(cudaStreamSynchronize(c->stream));
   double t[PH_F0 + 4] = {0};
-  for (auto& m : marks) {
+  for (auto& m : ph.marks) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, m.e0, m.e1) == cudaSuccess) t[m.phase] += ms;
-    cudaEventDestroy(m.e0);
-    cudaEventDestroy(m.e1);
   }
   res->t_heatbath_ms = t[PH_HB];
   res->t_hamiltonian_ms = t[PH_H];
   res->t_T_ms = t[PH_T];
   res->t_gauge_force_ms = t[PH_GF];
   for (int g = 0; g < 4; ++g) res->t_force_group_ms[g] = t[PH_F0 + g];
+  return WD_OK;
+}
+
+int hmc_trajectory_host(wd_ctx* c, const wd_hmc_params* p, double u, const double* U_in, double* U_out,
+                        wd_hmc_result* res) {
+  if (!c || !p || !res || !U_in || !U_out) return fail(WD_ERR_ARG, "null argument");
+  const size_t bytes = sizeof(double) * 72 * (size_t)c->g.V;
+  if (!c->lex_stage) WD_CUDA(cudaMalloc(&c->lex_stage, bytes));
+  WD_CUDA(cudaMemcpyAsync(c->lex_stage, U_in, bytes, cudaMemcpyHostToDevice, c->stream));
+  WD_TRY(wd_gauge_load(c, c->lex_stage));
+  WD_TRY(hmc_trajectory(c, p, u, res));
+  WD_TRY(wd_gauge_store(c, c->lex_stage));
+  WD_CUDA(cudaMemcpyAsync(U_out, c->lex_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
   return WD_OK;
 }
 

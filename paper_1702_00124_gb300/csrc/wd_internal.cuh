@@ -439,6 +439,7 @@ struct wd_ctx {
   int resid_dd = 0;                 // residual recomputation in double-float
   double2* gauge_backup = nullptr;  // FP64 links at the start of a trajectory
   double* mom = nullptr;            // momenta of a trajectory [4][2][8][Vh]
+  double* lex_stage = nullptr;      // lexicographic FP64 links, staging of host-buffer calls
   // reduction scratch
   double* red_partial = nullptr;
   unsigned* red_counter = nullptr;

@@ -59,9 +59,15 @@ class wd_hmc_params(C.Structure):
                 ("seed", C.c_uint64), ("traj_index", C.c_uint64)]
 
 
+class wd_integrate_params(C.Structure):
+    _fields_ = [("nterms", C.c_int), ("terms", C.POINTER(wd_term)), ("term_group", C.POINTER(C.c_int)),
+                ("phi", C.POINTER(C.c_void_p)), ("beta", C.c_double), ("nops", C.c_int),
+                ("ops", C.POINTER(wd_op)), ("cg_md", wd_cg_params), ("force_prec", C.c_int)]
+
+
 class wd_cost_result(C.Structure):
     _fields_ = [("C", C.c_double), ("p_acc", C.c_double), ("p_acc_est", C.c_double), ("mean_nmat", C.c_double),
-                ("exp_mdH", C.c_double), ("exp_mdH_err", C.c_double)]
+                ("exp_mdH", C.c_double), ("exp_mdH_err", C.c_double), ("C_est", C.c_double)]
 
 
 class wd_hmc_result(C.Structure):
@@ -104,6 +110,8 @@ _SIG = {
     "metropolis": ([_D, _D, C.POINTER(_I)], _I),
     "wd_cost": ([C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_D), _I, C.POINTER(wd_cost_result)], _I),
     "hmc_trajectory": ([_P, C.POINTER(wd_hmc_params), _D, C.POINTER(wd_hmc_result)], _I),
+    "hmc_trajectory_host": ([_P, C.POINTER(wd_hmc_params), _D, _P, _P, C.POINTER(wd_hmc_result)], _I),
+    "integrate": ([_P, _P, C.POINTER(wd_integrate_params), C.POINTER(_I)], _I),
     "wd_schedule_nested": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I, C.POINTER(_I)], _I),
     "wd_schedule_generalised": ([_I, _D, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(wd_op), _I,
                                  C.POINTER(_I)], _I),
@@ -147,6 +155,18 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, n):
+    """Address of a HOST float64 buffer of at least n elements (CPU tensor or numpy array)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() < n:
+            raise ValueError(f"expected a contiguous CPU float64 tensor of >= {n} elements")
+        return C.c_void_p(a.data_ptr())
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size < n:
+        raise ValueError(f"expected a contiguous float64 array of >= {n} elements")
+    return C.c_void_p(a.ctypes.data)
 
 
 def cg_params(tol=1e-10, maxiter=10000, prec=F64, delta=0.0, check_every=0):
@@ -392,9 +412,40 @@ class Lattice:
                           traj_index)
         r = wd_hmc_result()
         _check(lib.hmc_trajectory(self.h, C.byref(p), u, C.byref(r)))
+        return self._result(r)
+
+    @staticmethod
+    def _result(r):
         out = {k: getattr(r, k) for k, _ in wd_hmc_result._fields_}
         out["t_force_group_ms"] = list(r.t_force_group_ms)
         return out
+
+    def hmc_trajectory_host(self, terms, groups, beta, ops, cg_md, cg_acc, force_prec, seed, traj_index, u,
+                            U_in, U_out):
+        """hmc_trajectory with the links in and out through HOST buffers (CPU
+        float64 tensors or arrays of V * 72 doubles; pinned memory for DMA)."""
+        tarr = (wd_term * max(len(terms), 1))(*terms)
+        garr = (C.c_int * max(len(groups), 1))(*groups)
+        oarr = _ops_array(ops)
+        p = wd_hmc_params(len(terms), tarr, garr, beta, len(ops), oarr, cg_md, cg_acc, force_prec, seed,
+                          traj_index)
+        r = wd_hmc_result()
+        _check(lib.hmc_trajectory_host(self.h, C.byref(p), u, _host_ptr(U_in, self.V * 72),
+                                       _host_ptr(U_out, self.V * 72), C.byref(r)))
+        return self._result(r)
+
+    def integrate(self, P, terms, groups, phis, beta, ops, cg_md, force_prec):
+        """The integrator alone on caller-held momenta P (device algebra field),
+        pseudofermions phis (device half spinors) fixed; returns the number of
+        force evaluations."""
+        tarr = (wd_term * max(len(terms), 1))(*terms)
+        garr = (C.c_int * max(len(groups), 1))(*groups)
+        parr = (C.c_void_p * max(len(phis), 1))(*[_ptr(f) for f in phis])
+        oarr = _ops_array(ops)
+        p = wd_integrate_params(len(terms), tarr, garr, parr, beta, len(ops), oarr, cg_md, force_prec)
+        nf = C.c_int(0)
+        _check(lib.integrate(self.h, _ptr(P), C.byref(p), C.byref(nf)))
+        return nf.value
 
     def wd_nmat(self, reset=False):
         n = C.c_longlong(0)

@@ -88,6 +88,56 @@ def test_fermion_force(setup, kind):
     assert np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) < 1e-9 * np.linalg.norm(F_ref)
 
 
+# The filter of the trajectory bench (degree 24 on [0.005, 8]: ceil(sqrt(24)) = 5
+# checkpoint segments of five roots, the fused FP32 Chebyshev-step hop) and the
+# two-filter pair P_24 / P_4 of Section 3.3, at the bench's heavy kappa.
+BENCH_POLY, BENCH_LO, BENCH_KAPPA_H = (24, 0.005, 8.0), (4, 0.005, 8.0), 0.128
+
+
+@pytest.mark.parametrize("kind", ["poly", "filtered", "ratio"])
+def test_fermion_force_bench_filter(setup, kind):
+    """fermion_force (solve and force) and fermion_force_xy (force from the
+    oracle's X, no solve) against the oracle force at the bench's filter:
+    FP64 1e-9, FP32 1e-5 (relative, Frobenius)."""
+    from oracle.cg import cg
+    from oracle.poly import RatioFilter
+    s = setup
+    lat, gu, wd = s["lat"], s["gu"], s["wd"]
+    U, phi, kh = s["U"], s["chi"], BENCH_KAPPA_H
+    pf = ChebyshevFilter(*BENCH_POLY)
+    if kind == "poly":
+        t_o, t_g = actions.term("poly", kh, poly=pf), wd.term(wd.POLY, kh, poly=BENCH_POLY)
+    elif kind == "filtered":
+        t_o, t_g = actions.term("filtered", kh, poly=pf), wd.term(wd.FILTERED, kh, poly=BENCH_POLY)
+    else:
+        q = RatioFilter(pf, ChebyshevFilter(*BENCH_LO))
+        t_o = actions.term("ratio", kh, poly=q)
+        t_g = wd.term(wd.RATIO, kh, poly=BENCH_POLY, poly_lo=BENCH_LO)
+    phi_e = gu.pack(lat, phi, 0)
+    X_e = None
+    if kind == "filtered":
+        # The FP64 root product of K_hat P(K_hat) at degree 24 is accurate to about
+        # 1e-12 relative, so the oracle solves to 5e-12 (bounded iterations); the
+        # force error this leaves is of the same order, far below 1e-9.
+        X, info = cg(actions.filtered_op(U, kh, pf), phi, 5e-12, maxiter=400)
+        assert info["rel_resid"] <= 5e-12, info
+        F_ref = -force.poly_force(U, kh, pf.roots_times_x(), pf.scale(), X)
+        X_e = gu.pack(lat, X, 0)
+    else:
+        F_ref = force.fermion_force(U, t_o, phi)
+    nref = np.linalg.norm(F_ref)
+    for prec, tol in ((0, 1e-9), (1, 1e-5)):
+        F = lat.algebra_field()
+        lat.fermion_force(t_g, phi_e, wd.cg_params(tol=1e-12 if prec == 0 else 1e-10, prec=prec, maxiter=4000),
+                          1.0, F)
+        err = np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) / nref
+        assert err < tol, ("fermion_force", prec, err)
+        F = lat.algebra_field()
+        lat.fermion_force_xy(t_g, phi_e, X_e, None, prec, 1.0, F)
+        err = np.linalg.norm(gu.alg_to_host(lat, F) - F_ref) / nref
+        assert err < tol, ("fermion_force_xy", prec, err)
+
+
 def test_ratio_degenerate_and_invalid(setup):
     """Q = P / P = 1: S = phi^dag phi, phi = chi, zero force.  Filters whose orders
     do not nest ((n_lo + 1) not dividing (n + 1)) or whose intervals differ are
@@ -347,4 +397,78 @@ def test_ratio_heatbath_wide_filters_mixed_precision():
     S = lat.pf_action(t, phi, wd.cg_params(tol=1e-12))
     chi2 = float((chi * chi).sum())
     assert abs(S - chi2) < 1e-8 * chi2, (S, chi2)
+    lat.close()
+
+
+def test_integrate_on_caller_momenta():
+    """integrate() (Section 2: T[eps] and S[eps]; Section 3.2: nested schedule) on
+    caller-held momenta and pseudofermions, every step in FP64, against the
+    oracle's integrator from the same links, momenta and phi: final links 1e-10,
+    final momenta 1e-9 relative to max |P|."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 4)
+    U0 = synthetic.gauge_field(dims, 0.3, 931)
+    P0 = synthetic.momenta(dims, 932)
+    k, kh, beta, tau = 0.124, 0.115, 5.6, 0.3
+    pf = ChebyshevFilter(*POLY)
+    terms_o = [actions.term("hasenbusch", k, kh), actions.term("poly", kh, poly=pf)]
+    terms_g = [wd.term(wd.HASENBUSCH, k, kh), wd.term(wd.POLY, kh, poly=POLY)]
+    phis = [lattice.mask(synthetic.spinor_field(dims, 933 + i), dims, 0) for i in range(2)]
+    groups = [0, 1]
+    levels = [(0, 2), (1, 1), (-1, 2)]
+
+    def fog(grp, U):
+        if grp == -1:
+            return force.gauge_force(U, beta)
+        return sum(force.fermion_force(U, t, ph) for t, ph, g in zip(terms_o, phis, groups) if g == grp)
+
+    U1, P1 = hmc.integrate(U0, P0, hmc.nested(levels, tau, "omelyan"), fog)
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(gu.dev(U0))
+    Pe = gu.alg_to_dev(lat, P0)
+    phis_e = [gu.pack(lat, ph, 0) for ph in phis]
+    ops = wd.wd_schedule_nested(1, tau, [g for g, _ in levels], [n for _, n in levels])
+    nf = lat.integrate(Pe, terms_g, groups, phis_e, beta, ops, wd.cg_params(tol=1e-14, maxiter=20000), wd.F64)
+    assert nf > 0
+    Ub = torch.zeros(2 * U0.size, dtype=torch.float64, device="cuda")
+    lat.wd_gauge_store(Ub)
+    assert np.max(np.abs(gu.host_c(Ub, U0.shape) - U1)) < 1e-10
+    assert np.max(np.abs(gu.alg_to_host(lat, Pe) - P1)) < 1e-9 * np.max(np.abs(P1))
+    with pytest.raises(wd.WdError):        # an op kind other than T or S
+        lat.integrate(Pe, terms_g, groups, phis_e, beta, [(2, 0, 0.1)], wd.cg_params(), wd.F64)
+    lat.close()
+
+
+def test_trajectory_host_buffers_match_device():
+    """hmc_trajectory_host (links in and out through host memory, one copy each
+    way) gives the trajectory hmc_trajectory gives on the same links and draws."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    dims = (4, 4, 4, 4)
+    U0 = synthetic.gauge_field(dims, 0.3, 941)
+    k, kh, beta, tau = 0.124, 0.115, 5.6, 0.4
+    terms = [wd.term(wd.POLY, kh, poly=POLY), wd.term(wd.HASENBUSCH, k, kh)]
+    groups = [1, 0]
+    ops = wd.wd_schedule_nested(1, tau, [0, 1, -1], [2, 1, 2])
+    p32 = wd.cg_params(tol=1e-10, prec=wd.F32, maxiter=20000)
+    lat = wd.Lattice(dims)
+    lat.wd_set_autotune(0)
+    lat.wd_gauge_load(gu.dev(U0))
+    r_dev = lat.hmc_trajectory(terms, groups, beta, ops, p32, p32, wd.F32, 55, 1, 0.25)
+    Ub = torch.zeros(2 * U0.size, dtype=torch.float64, device="cuda")
+    lat.wd_gauge_store(Ub)
+    U_host = torch.from_numpy(np.ascontiguousarray(U0).view(np.float64).reshape(-1).copy()).pin_memory()
+    U_out = torch.zeros_like(U_host).pin_memory()
+    r_host = lat.hmc_trajectory_host(terms, groups, beta, ops, p32, p32, wd.F32, 55, 1, 0.25, U_host, U_out)
+    assert abs(r_host["dH"] - r_dev["dH"]) <= 1e-12 * max(1.0, abs(r_dev["dH"]))
+    assert r_host["accepted"] == r_dev["accepted"] and r_host["n_mat"] == r_dev["n_mat"]
+    assert np.max(np.abs(U_out.numpy() - Ub.cpu().numpy())) < 1e-13
+    U_in_place = U_host.clone().pin_memory()       # U_out may be U_in
+    lat.hmc_trajectory_host(terms, groups, beta, ops, p32, p32, wd.F32, 55, 1, 0.25, U_in_place, U_in_place)
+    assert np.max(np.abs(U_in_place.numpy() - Ub.cpu().numpy())) < 1e-13
+    with pytest.raises(ValueError):               # device tensors are not host buffers
+        lat.hmc_trajectory_host(terms, groups, beta, ops, p32, p32, wd.F32, 55, 1, 0.25, Ub, Ub)
     lat.close()

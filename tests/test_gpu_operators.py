@@ -78,7 +78,7 @@ def test_khat(setup, prec):
     eo = gu.pack(lat, psi, 0)
     out = lat.half_spinor()
     lat.mdagm_apply(k, prec, 1, eo, out)
-    assert gu.site_rel_err(gu.unpack(lat, out, 0), ref, 0, dims) < 2 * TOL[prec]
+    assert gu.site_rel_err(gu.unpack(lat, out, 0), ref, 0, dims) < TOL[prec]
 
 
 def test_khat_recon12(setup):
