@@ -12,9 +12,12 @@ true residual, FP64 links, momenta and H).
 
 Prints one JSON line.  `value` = trajectories per second (whole job);
 `roofline` = the FP32 hop stencil (the dominant kernel) sampled with CUDA
-events inside the timed region; `cpu_baseline` = the oracle's K_hat on a
-bounded sample, scaled to a trajectory by its K_hat count; `e2e` = the same
-trajectory through the C ABI from host buffers.
+events inside the timed region; `cpu_baseline` = the oracle timed on the host
+cores (per kernel on one core; one K_hat of the workload over every core,
+scaled to a trajectory by this run's K_hat count); `e2e` = the same
+trajectories through the C ABI's host-buffer call; `breakdown` = mixed vs FP64
+CG / force / trajectory at 32^3 x 64 and 16^3 x 32, the batched workload, and
+the error against the FP64 oracle of a solution, a force and a dH.
   --impl reference  times the oracle (the reference arm of this benchmark).
 Multi-GPU (torchrun): every rank runs an independent replica (different
 seed); value = all ranks' trajectories / max time.
@@ -24,8 +27,8 @@ import json
 import os
 import subprocess
 import sys
+import platform
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -49,10 +52,11 @@ LEVELS = [(0, 10), (1, 1), (-1, 2)]
 # double-float (2 x FP32, about 44-48 bits; b, x, r and dots stay FP64).
 # At this volume the double-float hop takes 0.50-0.58 ms against 2.08 ms in FP64.
 RESIDUAL_MODE = 1
-# K_hat applications of one trajectory of the default workload, counted by
-# the library's N_mat counter (algorithmic count; the reference arm scales
-# its per-K_hat time by it).
-N_MAT_PER_TRAJ = 20305
+# K_hat applications of one trajectory of the default workload: the mean of the
+# library's N_mat counter over 20 trajectories of this seeded chain (20,256).  The
+# reference arm, which runs no GPU code, scales its per-K_hat time by it; the GPU
+# arm's CPU baseline uses the count of its own run.
+N_MAT_PER_TRAJ = 20256
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hop_f32_c5_32x32x32x64.md")
 
 
@@ -128,42 +132,174 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_khat_seconds(reps=2):
-    """Oracle K_hat on a 32^3 x 4 slab (the workload's spatial volume, 1/16 of its
-    sites), seconds per application scaled to the full 32^3 x 64 lattice."""
-    from oracle import lattice, wilson
+def host_info():
+    """Host description for the CPU legs: cores and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
+
+
+# ---------------------------------------------------------------------------
+# The oracle (FP64 numpy, as it stands) timed on the host cores.  Workers are
+# spawned processes (the parent may hold a CUDA context) and import only numpy
+# and the oracle.  A c5 K_hat's work is done as 16 slabs of 32^3 x 4 sites (the
+# workload's spatial volume, 1/16 of its sites), one per task.
+SLAB = (32, 32, 32, 4)
+N_SLABS = 16
+_W = {}
+
+
+def _worker_init():
+    from oracle import lattice
     from paper_1702_00124_gb300 import synthetic
     w = WORKLOADS[DEFAULT_WORKLOAD]
-    slab = (32, 32, 32, 4)
-    U = synthetic.gauge_field(slab, w["a"], synthetic.SEED_BASE + 40)
-    psi = lattice.mask(synthetic.spinor_field(slab, synthetic.SEED_BASE + 41), slab, 0)
-    wilson.apply_Khat(U, psi, w["kappa"])          # warm
+    _W["U"] = synthetic.gauge_field(SLAB, w["a"], synthetic.SEED_BASE + 40)
+    _W["psi"] = lattice.mask(synthetic.spinor_field(SLAB, synthetic.SEED_BASE + 41), SLAB, 0)
+    _W["kappa"] = w["kappa"]
+
+
+def _slab_khat(_):
+    from oracle import wilson
     t = time.perf_counter()
+    wilson.apply_Khat(_W["U"], _W["psi"], _W["kappa"])
+    return time.perf_counter() - t
+
+
+def _single_thread_suite():
+    """Oracle per kernel on one core (seconds): K_hat at c1, c2, c3 and the c5 slab;
+    CG to a 1e-10 true residual at c1, c2; the plain-term force with its solve at c1
+    and the force from given X, Y at c3.  Also returns the c2 solution and the c1 force
+    (the references of the GPU error legs)."""
+    from oracle import actions, force, lattice, wilson
+    from oracle.cg import cg
+    from paper_1702_00124_gb300 import synthetic
+    out, refs = {}, {}
+    for name in ("c1_4x4x4x4", "c2_8x8x8x16", "c3_16x16x16x32"):
+        w = synthetic.WORKLOADS[name]
+        dims, k = w["dims"], w["kappa"]
+        U = synthetic.gauge_field(dims, w["a"], w["seed"])
+        chi = lattice.mask(synthetic.spinor_field(dims, w["seed"] + 100), dims, 0)
+        t = time.perf_counter()
+        wilson.apply_Khat(U, chi, k)
+        out[f"khat_{name}_s"] = time.perf_counter() - t
+        b = wilson.apply_Mhat(U, chi, k, dagger=True)
+        if name != "c3_16x16x16x32":
+            t = time.perf_counter()
+            X, info = cg(actions.K_op(U, k), b, 1e-10)
+            out[f"cg_{name}_s"] = time.perf_counter() - t
+            out[f"cg_{name}_iters"] = info["iters"]
+            refs[f"X_{name}"] = X
+        if name == "c1_4x4x4x4":
+            t = time.perf_counter()
+            refs["F_c1"] = force.fermion_force(U, actions.term("plain", k), b, tol=1e-12)
+            out["force_plain_c1_s"] = time.perf_counter() - t
+        if name == "c3_16x16x16x32":
+            Y = wilson.apply_Mhat(U, chi, k)
+            t = time.perf_counter()
+            -2 * force._dre_mhat(U, Y, chi, k)
+            out["force_xy_c3_s"] = time.perf_counter() - t
+    out["khat_c5_slab_s"] = (_worker_init(), _slab_khat(0))[1]
+    return out, refs
+
+
+def _oracle_dH_c1():
+    """dH of one FP64 oracle trajectory at 4^4 (the error leg's reference)."""
+    from oracle import actions, force, hmc, lattice, philox
+    from oracle.poly import ChebyshevFilter
+    from paper_1702_00124_gb300 import synthetic
+    c = DH_LEG
+    U0 = synthetic.gauge_field(c["dims"], c["a"], c["seed"])
+    pf = ChebyshevFilter(*c["poly"])
+    terms = [actions.term("poly", c["kappa_h"], poly=pf), actions.term("filtered", c["kappa_h"], poly=pf),
+             actions.term("hasenbusch", c["kappa"], c["kappa_h"])]
+    V = int(np.prod(c["dims"]))
+    base = c["traj"] * 64
+    P0 = philox.gaussian_field(V * 32, c["draw_seed"], base).reshape(lattice.shape(c["dims"]) + (4, 8))
+    phis = []
+    for i, t in enumerate(terms):
+        g = philox.gaussian_field(V * 24, c["draw_seed"], base + 1 + i)
+        chi = lattice.mask(g.view(np.complex128).reshape(lattice.shape(c["dims"]) + (4, 3)), c["dims"], 0)
+        phis.append(actions.heatbath(U0, t, chi / np.sqrt(2), tol=1e-12))
+
+    def H(U, P):
+        return hmc.kinetic(P) + force.gauge_action(U, c["beta"]) + sum(
+            actions.action(U, t, ph, tol=1e-12)[0] for t, ph in zip(terms, phis))
+
+    def fog(grp, U):
+        if grp == -1:
+            return force.gauge_force(U, c["beta"])
+        return sum(force.fermion_force(U, t, ph, tol=1e-12) for t, ph, g in zip(terms, phis, c["groups"])
+                   if g == grp)
+
+    U1, P1 = hmc.integrate(U0, P0, hmc.nested(c["levels"], c["tau"], "omelyan"), fog)
+    return H(U1, P1) - H(U0, P0)
+
+
+# The dH error leg: PF-MP + gauge at 4^4 with the trajectory bench's structure
+DH_LEG = dict(dims=(4, 4, 4, 4), a=0.3, seed=951, kappa=0.124, kappa_h=0.115, beta=5.6, tau=0.5,
+              poly=(8, 0.02, 6.0), groups=[1, 0, 0], levels=[(0, 3), (1, 1), (-1, 2)], draw_seed=321, traj=2)
+
+
+def spawn_pool(n):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n, initializer=_worker_init)
+
+
+def c5_khat_all_cores(pool, reps=1):
+    """Wall time of one c5 K_hat's work (16 slab applications) over the pool."""
+    best = None
     for _ in range(reps):
-        wilson.apply_Khat(U, psi, w["kappa"])
-    per = (time.perf_counter() - t) / reps
-    scale = np.prod(w["dims"]) / np.prod(slab)
-    return per * scale, f"oracle K_hat on a 32x32x32x4 slab ({reps} applications, x{scale:.0f} volume)"
+        t = time.perf_counter()
+        pool.map(_slab_khat, range(N_SLABS), chunksize=1)
+        dt = time.perf_counter() - t
+        best = dt if best is None else min(best, dt)
+    return best
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle on the host cores.  One step = one K_hat of the
+    32^3 x 64 workload (16 slab applications spread over every core), the unit of the
+    cost metric (Section 3.1); a trajectory is N_MAT_PER_TRAJ of them, which sets
+    `value`.  ms_per_step is the step's own measured time."""
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    steps = []
-    sample = ""
-    for i in range(args.warmup + args.steps):
-        per_khat, sample = oracle_khat_seconds(reps=1)
-        if i >= args.warmup:
-            steps.append(per_khat * N_MAT_PER_TRAJ)
-    t_traj = float(np.mean(steps))
-    value = 1.0 / t_traj
+    host = host_info()
+    n = host["nproc"] or 1
+    pool = spawn_pool(min(n, N_SLABS))
+    try:
+        for _ in range(args.warmup):
+            c5_khat_all_cores(pool)
+        steps = [c5_khat_all_cores(pool) for _ in range(args.steps)]
+    finally:
+        pool.close()
+        pool.join()
+    t_step = float(np.mean(steps))
+    value = 1.0 / (t_step * N_MAT_PER_TRAJ)
+    sample = (f"one K_hat of {args.workload} per step (16 slabs of 32x32x32x4 over {min(n, N_SLABS)} "
+              f"processes); value scaled by N_mat = {N_MAT_PER_TRAJ} K_hat per trajectory")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_traj * 1e3,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "dims": list(w["dims"])},
-            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
-                             "sample": sample + f", scaled by N_mat = {N_MAT_PER_TRAJ} K_hat per trajectory"},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": min(n, N_SLABS), "kind": "oracle",
+                             "sample": sample, "host": host},
             "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -250,6 +386,235 @@ def kernel_case(args):
     print(f"kernel case {args.kernel_case} on {args.workload}: {args.reps} K_hat applications")
 
 
+def e2e_run(lat, w, terms, groups, ops, cg_md, cg_acc, force_prec, seed, traj, n=2):
+    """The same trajectories end to end through the C ABI's host-buffer call
+    (hmc_trajectory_host): every trajectory copies the links in from pinned host
+    memory and back out, continuing the chain of the timed region."""
+    import torch
+    from paper_1702_00124_gb300 import synthetic
+    V = int(np.prod(w["dims"]))
+    U_dev = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+    lat.wd_gauge_store(U_dev)
+    U_host = U_dev.cpu().pin_memory()
+    del U_dev
+    dH = []
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(n):
+        u = synthetic.uniform(seed + traj[0])
+        r = lat.hmc_trajectory_host(terms, groups, w["beta"], ops, cg_md, cg_acc, force_prec, seed, traj[0], u,
+                                    U_host, U_host)
+        traj[0] += 1
+        dH.append(float(r["dH"]))
+    dt = time.perf_counter() - t
+    nbytes = V * 72 * 8
+    return {"value": n / dt, "unit": "trajectories/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "trajectories": n, "dH": dH,
+            "call": "hmc_trajectory_host (links in and out through pinned host memory, one cudaMemcpyAsync each way)"}
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t, out
+
+
+def breakdown_c5(lat, w, terms):
+    """At 32^3 x 64: one CG solve and one force of the Hasenbusch term in FP64, mixed
+    FP32 (FP64 and double-float residuals) and mixed BF16 to 1e-10; one filtered solve;
+    stand-alone K_hat bandwidth per precision."""
+    from paper_1702_00124_gb300 import wdhmc as wd
+    extras = {}
+    chi = lat.half_spinor()
+    lat.gaussian_draw(0, 0, 7, 7, chi)
+    b = lat.half_spinor()
+    lat.wd_apply(w["kappa"], True, wd.F64, chi, b)
+    F = lat.algebra_field()
+    runs = (("fp64", wd.F64, 0), ("mixed_fp32_fp64resid", wd.F32, 0), ("mixed_fp32", wd.F32, RESIDUAL_MODE),
+            ("mixed_bf16", wd.BF16, RESIDUAL_MODE))
+    for name, prec, rmode in runs:
+        lat.wd_set_residual(rmode)
+        x = lat.half_spinor()
+        dt, info = _timed(lambda: lat.cg_solve(w["kappa"], b, x, wd.cg_params(tol=1e-10, prec=prec, maxiter=20000)))
+        extras[f"cg_{name}"] = {"s": dt, "iters": info["iters"], "reliable_updates": info["reliable_updates"],
+                                "true_rel_resid": info["true_rel_resid"]}
+        if name in ("fp64", "mixed_fp32"):
+            dt, _ = _timed(lambda: lat.fermion_force(terms[2], chi, wd.cg_params(tol=1e-10, prec=prec), 1.0, F))
+            extras[f"force_hasenbusch_{name}"] = {"s": dt}
+        if name in ("mixed_fp32_fp64resid", "mixed_fp32"):
+            x = lat.half_spinor()
+            dt, info = _timed(lambda: lat.cg_solve(w["kappa_h"], b, x, wd.cg_params(tol=1e-10, prec=prec),
+                                                   filt=w["poly"]))
+            extras[f"filtered_cg_{name}"] = {"s": dt, "iters": info["iters"],
+                                             "reliable_updates": info["reliable_updates"],
+                                             "true_rel_resid": info["true_rel_resid"]}
+    lat.wd_set_residual(RESIDUAL_MODE)
+    out = lat.half_spinor()
+    for name, prec, recon in (("fp64", wd.F64, 0), ("double_float", wd.DF, 0), ("fp32", wd.F32, 0),
+                              ("fp32_recon12", wd.F32, 1), ("bf16_recon12", wd.BF16, 1)):
+        lat.wd_set_recon(recon)
+        lat.wd_profile_enable(1)
+        lat.mdagm_apply(w["kappa"], prec, 1, chi, out)
+        lat.wd_profile_enable(1)
+        for _ in range(10):
+            lat.mdagm_apply(w["kappa"], prec, 1, chi, out)
+        pr = lat.wd_profile_read(prec)
+        extras[f"hop_{name}"] = {"GBs": pr["bytes"] / (pr["ms"] * 1e-3) / 1e9,
+                                 "ms_per_hop": pr["ms"] / max(pr["launches"], 1)}
+    lat.wd_set_recon(wd.RECON_12)
+    lat.wd_profile_enable(0)
+    return extras
+
+
+def c3_legs(wd):
+    """The paper's volume, 16^3 x 32, with the bench's PF-MP action: one trajectory,
+    one CG solve and one force in plain FP64 and in the mixed-precision form (FP32 bulk,
+    12-real links, double-float residuals, FP32 forces; the autograd adjoint for the
+    force), all to a 1e-10 true residual."""
+    import torch
+    from paper_1702_00124_gb300 import synthetic
+    from paper_1702_00124_gb300.autograd import pf_action
+    w = WORKLOADS["c3_16x16x16x32"]
+    seed = synthetic.SEED_BASE + 2
+    U = synthetic.gauge_field(w["dims"], w["a"], seed)
+    U_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+    lat = wd.Lattice(w["dims"])
+    terms = [wd.term(wd.POLY, w["kappa_h"], poly=w["poly"]), wd.term(wd.FILTERED, w["kappa_h"], poly=w["poly"]),
+             wd.term(wd.HASENBUSCH, w["kappa"], w["kappa_h"])]
+    groups = [1, 0, 0]
+    ops = wd.wd_schedule_nested(1, w["tau"], [g for g, _ in LEVELS], [n for _, n in LEVELS])
+    out = {}
+    modes = {"mixed": dict(recon=wd.RECON_12, resid=RESIDUAL_MODE, prec=wd.F32, fprec=wd.F32),
+             "fp64": dict(recon=wd.RECON_18, resid=0, prec=wd.F64, fprec=wd.F64)}
+    for name, m in modes.items():
+        lat.wd_set_recon(m["recon"])
+        lat.wd_set_residual(m["resid"])
+        p = wd.cg_params(tol=1e-10, prec=m["prec"], maxiter=20000)
+        recs = []
+        for i in range(2 if name == "mixed" else 1):      # mixed: the first one warms up
+            lat.wd_gauge_load(U_dev)
+            dt, r = _timed(lambda: lat.hmc_trajectory(terms, groups, w["beta"], ops, p, p, m["fprec"], seed, 0, 0.5))
+            recs.append((dt, r))
+        dt, r = recs[-1]
+        out[f"trajectory_{name}"] = {"s": dt, "dH": r["dH"], "n_mat": r["n_mat"], "force_evals": r["n_force_evals"]}
+        lat.wd_gauge_load(U_dev)
+        chi = lat.half_spinor()
+        lat.gaussian_draw(0, 0, seed, 100, chi)
+        b = lat.half_spinor()
+        lat.wd_apply(w["kappa"], True, wd.F64, chi, b)
+        x = lat.half_spinor()
+        dt, info = _timed(lambda: lat.cg_solve(w["kappa"], b, x, p))
+        out[f"cg_hasenbusch_{name}"] = {"s": dt, "iters": info["iters"], "true_rel_resid": info["true_rel_resid"]}
+        F = lat.algebra_field()
+        dt, _ = _timed(lambda: lat.fermion_force(terms[2], chi, p, 1.0, F))
+        out[f"force_hasenbusch_{name}"] = {"s": dt}
+        wv = torch.zeros(64 * lat.Vh, dtype=torch.float64, device="cuda", requires_grad=True)
+        dt, _ = _timed(lambda: pf_action(wv, lat, terms[2], chi, p, m["fprec"]).backward())
+        out[f"autograd_force_hasenbusch_{name}"] = {"s": dt}
+    out["trajectory_dH_mixed_minus_fp64"] = out["trajectory_mixed"]["dH"] - out["trajectory_fp64"]["dH"]
+    lat.close()
+    return out
+
+
+def cpu_baseline(nmat):
+    """The oracle timed on the host cores (single-thread per kernel in one spawned
+    process, then one c5 K_hat's work over every core); value = trajectories/s of the
+    oracle at the all-core K_hat rate and this run's N_mat."""
+    host = host_info()
+    pool = spawn_pool(1)
+    try:
+        single, refs = pool.apply(_single_thread_suite)
+    finally:
+        pool.close()
+        pool.join()
+    n = min(host["nproc"] or 1, N_SLABS)
+    pool = spawn_pool(n)
+    try:
+        c5_khat_all_cores(pool)                        # warm
+        t_all = c5_khat_all_cores(pool, reps=2)
+    finally:
+        pool.close()
+        pool.join()
+    value = 1.0 / (t_all * nmat)
+    cpu = {"value": value, "unit": "trajectories/s", "cores": n, "kind": "oracle",
+           "sample": f"one K_hat of the 32^3 x 64 workload (16 slabs of 32x32x32x4 over {n} processes, "
+                     f"{t_all:.2f} s), scaled by this run's N_mat = {nmat:.0f} K_hat per trajectory",
+           "host": host, "c5_khat_all_cores_s": t_all,
+           "c5_khat_single_thread_s": single["khat_c5_slab_s"] * N_SLABS,
+           "per_kernel_single_thread_s": single}
+    return cpu, refs
+
+
+def error_legs(wd, refs, dH_ref):
+    """Error against the FP64 oracle, outside the timed region: the c2 CG solution
+    (FP64, mixed FP32, mixed BF16 at 1e-10), the c1 plain-term force (FP64, FP32) and
+    the dH of one c1 PF-MP trajectory (FP64, and the bench's mixed configuration)."""
+    import torch
+    from paper_1702_00124_gb300 import synthetic
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
+
+    def even_half(lat, lex):            # the library ignores the odd sites of lex
+        eo = lat.half_spinor()
+        lat.wd_spinor_pack(0, dev(lex), eo)
+        return eo
+
+    def rel(a, b):
+        return float(np.linalg.norm((a - b).reshape(-1)) / np.linalg.norm(b.reshape(-1)))
+
+    out = {}
+    w = synthetic.WORKLOADS["c2_8x8x8x16"]
+    dims, k = w["dims"], w["kappa"]
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(dev(synthetic.gauge_field(dims, w["a"], w["seed"])))
+    lat.wd_set_residual(RESIDUAL_MODE)
+    b = lat.half_spinor()
+    lat.wd_apply(k, True, wd.F64, even_half(lat, synthetic.spinor_field(dims, w["seed"] + 100)), b)
+    X_ref = refs["X_c2_8x8x8x16"]
+    for name, prec in (("fp64", wd.F64), ("mixed_fp32", wd.F32), ("mixed_bf16", wd.BF16)):
+        x = lat.half_spinor()
+        info = lat.cg_solve(k, b, x, wd.cg_params(tol=1e-10, prec=prec, maxiter=20000))
+        lex = torch.zeros(X_ref.size * 2, dtype=torch.float64, device="cuda")
+        lat.wd_spinor_unpack(0, x, lex)
+        got = lex.cpu().numpy().view(np.complex128).reshape(X_ref.shape)
+        out[f"c2_cg_solution_{name}"] = {"rel_err": rel(got, X_ref), "iters": info["iters"],
+                                         "true_rel_resid": info["true_rel_resid"]}
+    lat.close()
+    w = synthetic.WORKLOADS["c1_4x4x4x4"]
+    dims, k = w["dims"], w["kappa"]
+    lat = wd.Lattice(dims)
+    lat.wd_gauge_load(dev(synthetic.gauge_field(dims, w["a"], w["seed"])))
+    phi = lat.half_spinor()
+    lat.wd_apply(k, True, wd.F64, even_half(lat, synthetic.spinor_field(dims, w["seed"] + 100)), phi)
+    F_ref = refs["F_c1"]
+    for name, prec in (("fp64", wd.F64), ("mixed_fp32", wd.F32)):
+        F = lat.algebra_field()
+        lat.fermion_force(wd.term(wd.PLAIN, k), phi, wd.cg_params(tol=1e-10, prec=prec), 1.0, F)
+        lex = torch.zeros(F_ref.size, dtype=torch.float64, device="cuda")
+        lat.wd_algebra_unpack(F, lex)
+        out[f"c1_force_{name}"] = {"rel_err": rel(lex.cpu().numpy().reshape(F_ref.shape), F_ref)}
+    lat.close()
+    c = DH_LEG
+    U0 = synthetic.gauge_field(c["dims"], c["a"], c["seed"])
+    terms = [wd.term(wd.POLY, c["kappa_h"], poly=c["poly"]), wd.term(wd.FILTERED, c["kappa_h"], poly=c["poly"]),
+             wd.term(wd.HASENBUSCH, c["kappa"], c["kappa_h"])]
+    ops = wd.wd_schedule_nested(1, c["tau"], [g for g, _ in c["levels"]], [n for _, n in c["levels"]])
+    for name, prec, fprec, recon, resid in (("fp64", wd.F64, wd.F64, 0, 0), ("mixed", wd.F32, wd.F32, 1, 1)):
+        lat = wd.Lattice(c["dims"])
+        lat.wd_gauge_load(dev(U0))
+        lat.wd_set_recon(recon)
+        lat.wd_set_residual(resid)
+        p = wd.cg_params(tol=1e-12 if prec == wd.F64 else 1e-10, prec=prec, maxiter=20000)
+        r = lat.hmc_trajectory(terms, c["groups"], c["beta"], ops, p, p, fprec, c["draw_seed"], c["traj"], 0.0)
+        out[f"c1_trajectory_dH_{name}"] = {"dH": r["dH"], "dH_oracle": dH_ref, "abs_err": abs(r["dH"] - dH_ref)}
+        lat.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,6 +656,7 @@ def main():
     lat.wd_set_residual(RESIDUAL_MODE)
     U_dev = U_host.to("cuda", non_blocking=True)
     lat.wd_gauge_load(U_dev)
+    del U_dev
     terms = [wd.term(wd.POLY, w["kappa_h"], poly=w["poly"]), wd.term(wd.FILTERED, w["kappa_h"], poly=w["poly"]),
              wd.term(wd.HASENBUSCH, w["kappa"], w["kappa_h"])]
     groups = [1, 0, 0]
@@ -331,12 +697,14 @@ def main():
     nmat = (lat.wd_nmat() - n0) / args.steps
     prof = lat.wd_profile_read(wd.F32)
     prof64 = lat.wd_profile_read(wd.F64)
+    profdd = lat.wd_profile_read(wd.DF)
     counts = lat.wd_hop_counts()
     lat.wd_profile_enable(0)
     # share of the timed region spent in each hop family: all launches of the
     # family x its average sampled duration
     shares = {}
-    for name, pr, n in (("k_hop_fp32", prof, counts[wd.F32]), ("k_hop_fp64", prof64, counts[wd.F64])):
+    for name, pr, n in (("k_hop_fp32", prof, counts[wd.F32]), ("k_hop_fp64", prof64, counts[wd.F64]),
+                        ("k_hop_dd", profdd, counts[wd.DF])):
         if pr["launches"]:
             shares[name] = {"launches": n, "avg_ms": pr["ms"] / pr["launches"],
                             "share": n * pr["ms"] / pr["launches"] / (elapsed * 1e3)}
@@ -360,76 +728,17 @@ def main():
     e2e = None
     cpu = None
     if rank == 0 and not args.no_extras:
-        # end to end through the C ABI from pinned host buffers, one trajectory
-        out_host = torch.empty_like(U_host).pin_memory()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        U_dev.copy_(U_host, non_blocking=True)
-        lat.wd_gauge_load(U_dev)
-        r = trajectory()
-        lat.wd_gauge_store(U_dev)
-        out_host.copy_(U_dev, non_blocking=True)
-        torch.cuda.synchronize()
-        dh = float(r["dH"])
-        t_e2e = time.perf_counter() - t
-        nbytes = U_host.numel() * 8
-        e2e = {"value": 1.0 / t_e2e, "unit": "trajectories/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes + 8, "dH": dh}
-        # mixed vs FP64: one CG solve and one force evaluation of the Hasenbusch term
-        chi = lat.half_spinor()
-        lat.gaussian_draw(0, 0, 7, 7, chi)
-        b = lat.half_spinor()
-        lat.wd_apply(w["kappa"], True, wd.F64, chi, b)
-        F = lat.algebra_field()
-        runs = (("fp64", wd.F64, 0), ("mixed_fp32_fp64resid", wd.F32, 0), ("mixed_fp32", wd.F32, RESIDUAL_MODE),
-                ("mixed_bf16", wd.BF16, RESIDUAL_MODE))
-        for name, prec, rmode in runs:
-            lat.wd_set_residual(rmode)
-            x = lat.half_spinor()
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            info = lat.cg_solve(w["kappa"], b, x, wd.cg_params(tol=1e-10, prec=prec, maxiter=20000))
-            torch.cuda.synchronize()
-            extras[f"cg_{name}"] = {"s": time.perf_counter() - t, "iters": info["iters"],
-                                    "reliable_updates": info["reliable_updates"],
-                                    "true_rel_resid": info["true_rel_resid"]}
-            if name in ("fp64", "mixed_fp32"):
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-                lat.fermion_force(terms[2], chi, wd.cg_params(tol=1e-10, prec=prec), 1.0, F)
-                torch.cuda.synchronize()
-                extras[f"force_hasenbusch_{name}"] = {"s": time.perf_counter() - t}
-            # the filtered term's solve: the FP64-residual cost centre
-            if name in ("mixed_fp32_fp64resid", "mixed_fp32"):
-                x = lat.half_spinor()
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-                info = lat.cg_solve(w["kappa_h"], b, x, wd.cg_params(tol=1e-10, prec=prec), filt=w["poly"])
-                torch.cuda.synchronize()
-                extras[f"filtered_cg_{name}"] = {"s": time.perf_counter() - t, "iters": info["iters"],
-                                                 "reliable_updates": info["reliable_updates"],
-                                                 "true_rel_resid": info["true_rel_resid"]}
-        lat.wd_set_residual(RESIDUAL_MODE)
-        # stand-alone K_hat bandwidth per precision (10 applications each)
-        out = lat.half_spinor()
-        for name, prec, recon in (("fp64", wd.F64, 0), ("double_float", wd.DF, 0), ("fp32", wd.F32, 0),
-                                  ("fp32_recon12", wd.F32, 1), ("bf16_recon12", wd.BF16, 1)):
-            lat.wd_set_recon(recon)
-            lat.wd_profile_enable(1)
-            lat.mdagm_apply(w["kappa"], prec, 1, chi, out)
-            lat.wd_profile_enable(1)
-            for _ in range(10):
-                lat.mdagm_apply(w["kappa"], prec, 1, chi, out)
-            pr = lat.wd_profile_read(prec)
-            extras[f"hop_{name}"] = {"GBs": pr["bytes"] / (pr["ms"] * 1e-3) / 1e9,
-                                     "ms_per_hop": pr["ms"] / max(pr["launches"], 1)}
-        lat.wd_set_recon(wd.RECON_12)
-        lat.wd_profile_enable(0)
+        e2e = e2e_run(lat, w, terms, groups, ops, cg_md, cg_acc, wd.F32, seed, traj)
+        pool = spawn_pool(1)
+        refs_job = pool.apply_async(_oracle_dH_c1)
+        extras.update(breakdown_c5(lat, w, terms))
+        extras["c3_16x16x16x32"] = c3_legs(wd)
         extras["batched_24_lattices_x4_rhs"] = batched_workload_run(wd)
-        per_khat, sample = oracle_khat_seconds(reps=2)
-        cpu_traj = per_khat * nmat
-        cpu = {"value": 1.0 / cpu_traj, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
-               "sample": sample + f", scaled by this run's N_mat = {nmat:.0f} K_hat per trajectory"}
+        dH_ref = refs_job.get()
+        pool.close()
+        pool.join()
+        cpu, refs = cpu_baseline(nmat)
+        extras["error_vs_fp64_oracle"] = error_legs(wd, refs, dH_ref)
 
     if rank == 0:
         acc = [int(r["accepted"]) for r in timed]
@@ -445,7 +754,7 @@ def main():
                                         + ("A x in double-float (2xFP32, ~48 bits)" if RESIDUAL_MODE else "A x in FP64")
                                         + "; links, momenta, H in FP64",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "working set (1.2 GB FP64 links + FP32 copies) far above the 126 MB L2"},
+                           "l2": "inputs larger than L2: working set (1.2 GB FP64 links + FP32 copies) far above the 129 MB L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "hop_time_shares": shares,
                 "clocks": clk,

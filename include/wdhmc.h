@@ -264,6 +264,10 @@ typedef struct {
   int force_prec;            /* arithmetic of force kernels (WD_F64 / WD_F32) */
   uint64_t seed;             /* Philox key for momenta and pseudofermions */
   uint64_t traj_index;       /* counter stream: trajectory number */
+  int h0_solve;              /* 0: the starting pseudofermion actions are the heat
+                                bath's sum_i chi_i^dag chi_i (exact up to the heat
+                                bath's solver tolerance); 1: each is re-evaluated by
+                                its solve, as the final ones always are */
 } wd_hmc_params;
 
 typedef struct {

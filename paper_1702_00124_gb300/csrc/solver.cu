@@ -164,7 +164,7 @@ int poly_apply_f(wd_ctx* c, double kappa, const wd_poly& P, int /*prec*/, const 
 
 // ----------------------------------------------------------------------------
 // operators for CG
-enum OpKind { OP_K = 0, OP_KP = 1, OP_P = 2, OP_R = 3 };
+enum OpKind { OP_K = 0, OP_KP = 1, OP_R = 3 };
 
 struct Op {
   OpKind kind;
@@ -183,9 +183,7 @@ static int op_apply(wd_ctx* c, const Op& op, const Field& in, const Field& out, 
     WD_TRY(apply_khat(c, op.kappa, in, out, t1, t2, in_cg, in_cg));
     return WD_OK;
   }
-  if (op.kind == OP_P) {
-    WD_TRY(poly_apply_f(c, op.kappa, op.poly, in.fmt, in, out));
-  } else if (op.kind == OP_R) {
+  if (op.kind == OP_R) {
     WD_TRY(roots_apply_f(c, op.kappa, *op.roots, in, out));
   } else {
     Field s;
@@ -230,14 +228,14 @@ static int true_residual(wd_ctx* c, const Op& op, const Field& b, const Field& x
 
 // Default reliable-update factor per sloppy precision: the iterated residual
 // of FP32 stays faithful over larger reductions than that of 16-bit storage.
-// The Chebyshev-recurrence operators (P, K P) are well conditioned, accurate
-// to a few u_FP32 in FP32, and their FP64 application costs n+1 FP64 K_hat, so
-// they recompute the residual less often.  The root product Q = P_2 / P_1 is
+// The Chebyshev-recurrence operator K P is well conditioned, accurate to a few
+// u_FP32 in FP32, and its FP64 application costs n+1 FP64 K_hat, so it
+// recomputes the residual less often.  The root product Q = P_2 / P_1 is
 // not: each real quadratic factor loses about u / |z|^2 on low modes, up to
 // 6e-5 relative for P_26 / P_8 on [0.005, 8], and a sloppy cycle asked to gain
 // 1e-5 stalls; it takes the K_hat factor.
 static double default_delta(int prec, OpKind kind) {
-  if ((kind == OP_KP || kind == OP_P) && prec == WD_F32) return 1e-5;
+  if (kind == OP_KP && prec == WD_F32) return 1e-5;
   switch (prec) {
     case WD_F32: return 1e-3;
     case WD_F16: return 5e-2;
@@ -352,15 +350,6 @@ int cg_solve_f(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, con
     WD_TRY(poly_coef(*filt, &pc));
   }
   return cg_core(c, op, b, x, p, info, x_zero);
-}
-
-// CG on P(K_hat) (heat bath of the polynomial term), from x = 0
-int cg_solve_poly(wd_ctx* c, double kappa, const wd_poly& P, const Field& b, const Field& x,
-                  const wd_cg_params& p, wd_cg_info* info) {
-  PolyCoef pc;
-  WD_TRY(poly_coef(P, &pc));
-  Op op{OP_P, kappa, P};
-  return cg_core(c, op, b, x, p, info, true);
 }
 
 // CG on Q(K_hat) (heat bath of the ratio term), from x = 0

@@ -275,12 +275,17 @@ int term_heatbath(wd_ctx* c, const wd_term& t, const Field& chi, const wd_cg_par
       WD_TRY(solve(c, t.kappa_h, nullptr, y, z, p));
       return mhat(c, t.kappa_h, false, z, phi);
     case WD_TERM_POLY: {
+      // phi = P^-1 C^dag chi = K [K P]^-1 C^dag chi (P and K commute): the filtered
+      // operator K P is close to 1 on [eps, lam], so its solve takes a few
+      // iterations where CG on P(K) itself, about as ill-conditioned as K, takes
+      // as many as a K solve, each n times dearer.  The same residual bound
+      // |C^dag chi - K P x| <= tol |C^dag chi| gives the same error in phi.
       PolyCoef pc;
       WD_TRY(poly_coef(t.poly, &pc));
+      WD_TRY(w.get(WD_F64, &z));
       WD_TRY(apply_cdag(c, t.kappa, pc, chi, y));
-      WD_TRY(zero(c, phi));
-      wd_cg_info info;
-      return cg_solve_poly(c, t.kappa, t.poly, y, phi, p, &info);
+      WD_TRY(solve(c, t.kappa, &t.poly, y, z, p));
+      return khat_hp(c, t.kappa, z, phi);
     }
     case WD_TERM_FILTERED: {
       PolyCoef pc;
@@ -731,15 +736,24 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
   // momenta and pseudofermions
   begin(PH_HB);
   WD_TRY(gaussian_draw_k(c, 1, 0, p->seed, base, c->mom));
+  double noise = 0.0;   // sum_i chi_i^dag chi_i
   for (int i = 0; i < p->nterms; ++i) {
     // chi ~ exp(-chi^dag chi) (Section 2): real and imaginary parts N(0, 1/2),
     // the unit-variance Philox draw scaled by 1/sqrt(2)
     WD_TRY(gaussian_draw_k(c, 0, 0, p->seed, base + 1 + i, (double*)chi.data));
     WD_TRY(axpby(c, M_SQRT1_2, chi, 0.0, chi, chi));
+    if (!p->h0_solve) {
+      double n2;
+      WD_TRY(norm2(c, chi, &n2));
+      noise += n2;
+    }
     WD_TRY(term_heatbath(c, p->terms[i], chi, p->cg_acc, phi[i]));
   }
   end();
-  auto hamiltonian = [&](double* H, double* SG) -> int {
+  // H = sum tr P^2 + S_G + sum_i S_i(phi_i).  At the start of the trajectory the
+  // heat bath fixes S_i(phi_i) = chi_i^dag chi_i (to the heat bath's solver
+  // tolerance), which replaces the solves unless h0_solve asks for them.
+  auto hamiltonian = [&](double* H, double* SG, bool from_noise) -> int {
     double k, s, sum;
     WD_TRY(kinetic_k(c, c->mom, &k));
     sum = k;
@@ -749,22 +763,26 @@ int hmc_trajectory(wd_ctx* c, const wd_hmc_params* p, double u, wd_hmc_result* r
       *SG = p->beta * s;
       sum += *SG;
     }
-    for (int i = 0; i < p->nterms; ++i) {
-      WD_TRY(term_action(c, p->terms[i], phi[i], p->cg_acc, &s));
-      sum += s;
+    if (from_noise) {
+      sum += noise;
+    } else {
+      for (int i = 0; i < p->nterms; ++i) {
+        WD_TRY(term_action(c, p->terms[i], phi[i], p->cg_acc, &s));
+        sum += s;
+      }
     }
     *H = sum;
     return WD_OK;
   };
   begin(PH_H);
-  WD_TRY(hamiltonian(&res->H0, &res->S_gauge0));
+  WD_TRY(hamiltonian(&res->H0, &res->S_gauge0, !p->h0_solve));
   end();
   int nf = 0;
   const int fprec = p->force_prec == WD_F64 ? WD_F64 : WD_F32;
   WD_TRY(run_ops(c, c->mom, p->nterms, p->terms, p->term_group, phi.data(), p->beta, p->nops, p->ops, md, fprec,
                  &nf, &ph));
   begin(PH_H);
-  WD_TRY(hamiltonian(&res->H1, &res->S_gauge1));
+  WD_TRY(hamiltonian(&res->H1, &res->S_gauge1, false));
   end();
   res->dH = res->H1 - res->H0;
   res->n_force_evals = nf;

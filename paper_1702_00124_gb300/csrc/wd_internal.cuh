@@ -535,8 +535,6 @@ int poly_apply_f(wd_ctx* c, double kappa, const wd_poly& P, int prec, const Fiel
 // x_zero: start from x = 0 (x is zeroed, the initial residual is b itself)
 int cg_solve_f(wd_ctx* c, double kappa, const wd_poly* filt, const Field& b, const Field& x,
                const wd_cg_params& p, wd_cg_info* info, bool x_zero = false);
-int cg_solve_poly(wd_ctx* c, double kappa, const wd_poly& P, const Field& b, const Field& x,
-                  const wd_cg_params& p, wd_cg_info* info);
 
 // kernels of other units
 int pack_k(wd_ctx* c, bool unpack, int nouter, int nchunk, int chunk, int parity, const double* src,

@@ -56,7 +56,7 @@ class wd_hmc_params(C.Structure):
     _fields_ = [("nterms", C.c_int), ("terms", C.POINTER(wd_term)), ("term_group", C.POINTER(C.c_int)),
                 ("beta", C.c_double), ("nops", C.c_int), ("ops", C.POINTER(wd_op)),
                 ("cg_md", wd_cg_params), ("cg_acc", wd_cg_params), ("force_prec", C.c_int),
-                ("seed", C.c_uint64), ("traj_index", C.c_uint64)]
+                ("seed", C.c_uint64), ("traj_index", C.c_uint64), ("h0_solve", C.c_int)]
 
 
 class wd_integrate_params(C.Structure):
@@ -404,12 +404,12 @@ class Lattice:
     def gaussian_draw(self, what, parity, seed, stream, out):
         _check(lib.gaussian_draw(self.h, what, parity, seed, stream, _ptr(out)))
 
-    def hmc_trajectory(self, terms, groups, beta, ops, cg_md, cg_acc, force_prec, seed, traj_index, u):
+    def hmc_trajectory(self, terms, groups, beta, ops, cg_md, cg_acc, force_prec, seed, traj_index, u, h0_solve=0):
         tarr = (wd_term * max(len(terms), 1))(*terms)
         garr = (C.c_int * max(len(groups), 1))(*groups)
         oarr = _ops_array(ops)
         p = wd_hmc_params(len(terms), tarr, garr, beta, len(ops), oarr, cg_md, cg_acc, force_prec, seed,
-                          traj_index)
+                          traj_index, h0_solve)
         r = wd_hmc_result()
         _check(lib.hmc_trajectory(self.h, C.byref(p), u, C.byref(r)))
         return self._result(r)
@@ -421,14 +421,14 @@ class Lattice:
         return out
 
     def hmc_trajectory_host(self, terms, groups, beta, ops, cg_md, cg_acc, force_prec, seed, traj_index, u,
-                            U_in, U_out):
+                            U_in, U_out, h0_solve=0):
         """hmc_trajectory with the links in and out through HOST buffers (CPU
         float64 tensors or arrays of V * 72 doubles; pinned memory for DMA)."""
         tarr = (wd_term * max(len(terms), 1))(*terms)
         garr = (C.c_int * max(len(groups), 1))(*groups)
         oarr = _ops_array(ops)
         p = wd_hmc_params(len(terms), tarr, garr, beta, len(ops), oarr, cg_md, cg_acc, force_prec, seed,
-                          traj_index)
+                          traj_index, h0_solve)
         r = wd_hmc_result()
         _check(lib.hmc_trajectory_host(self.h, C.byref(p), u, _host_ptr(U_in, self.V * 72),
                                        _host_ptr(U_out, self.V * 72), C.byref(r)))
