@@ -120,82 +120,112 @@ typedef struct {
 
 /* ---- context, fields ------------------------------------------------------ */
 
-/* Create a context for one lattice on the current device; stream may be NULL
- * (legacy default stream) or a cudaStream_t.  Allocates the workspaces. */
+/* Create a context for one lattice (Section 3.1: the lattice of the Wilson
+ * action; extents even for the even-odd split) on the current device; stream
+ * may be NULL (legacy default stream) or a cudaStream_t.  Allocates the link
+ * copies and reduction scratch; *out = NULL and WD_ERR_ARG on odd or < 2
+ * extents, WD_ERR_CUDA when an allocation fails. */
 int wd_context_create(const int dims[4], void* stream, wd_ctx** out);
+/* Synchronise the context's stream and free everything it allocated (no
+ * counterpart in the paper).  NULL is accepted. */
 int wd_context_destroy(wd_ctx* ctx);
-/* Message of the last error on the calling thread (static storage). */
+/* Message of the last error on the calling thread (static storage; no
+ * counterpart in the paper). */
 const char* wd_last_error(void);
-/* Low-precision link storage (enum wd_recon); takes effect at the next load. */
+/* Low-precision link storage (enum wd_recon) of the links U_mu(x) of the Wilson
+ * action (Section 3.1); a storage choice, takes effect at the next load. */
 int wd_set_recon(wd_ctx* ctx, int recon);
 /* Arithmetic of the residual recomputation r = b - A x inside mixed-precision
- * solves (the reliable updates): mode 0 = FP64 (default); mode 1 =
+ * solves of K (Section 2, the iterative solver; the precision is not the
+ * paper's, which states none): mode 0 = FP64 (default); mode 1 =
  * double-float, x split into two FP32 words and A applied with error-free
  * FP32 arithmetic (about 48 significant bits, 1e-14 relative; b, x, r, dots
  * stay FP64).  GB300 runs FP64 at 1/60 of its FP32 rate, and a filtered
  * operator's residual costs n+1 K_hat.  Mode 1 allocates a double-float copy
  * of the links (as much as the FP64 copy) on first use. */
 int wd_set_residual(wd_ctx* ctx, int mode);
-/* Launch-shape autotuner of the hop kernels (on by default): the first launch
+/* Launch-shape autotuner of the hop kernels (no counterpart in the paper; on
+ * by default): the first launch
  * of each (formats, link storage, dagger, epilogue) outside a queued CG chunk
  * times the candidate block sizes and register caps on the context stream and
  * keeps the fastest for the context's volume.  enable: 1 on, 0 off, -1 leave;
  * *n_tuned (may be NULL) = number of tuned keys. */
 int wd_set_autotune(wd_ctx* ctx, int enable, int* n_tuned);
-/* The index-th tuned entry: its key (((in*8 + out)*8 + y)*4 + links)*4 +
+/* The index-th tuned entry (no counterpart in the paper; WD_ERR_ARG when
+ * index is out of range): its key (((in*8 + out)*8 + y)*4 + links)*4 +
  * 2 dagger + xpay, with formats as enum wd_prec (y = 7 without epilogue) and
  * links 0 FP64, 1 FP32 18 reals, 2 FP32 12 reals, 3 double-float), the chosen
  * block size and the launch bound (128 or 256) the chosen kernel is compiled for. */
 int wd_tune_entry(wd_ctx* ctx, int index, long long* key, int* threads, int* maxt);
-/* Volume helpers: out[0] = V, out[1] = Vh. */
+/* Volume of the lattice (Section 3.1): out[0] = V, out[1] = Vh = V/2 sites per parity. */
 int wd_volume(const wd_ctx* ctx, long long out[2]);
 
-/* Load the gauge field from a lexicographic FP64 array (device); builds the
- * FP64 even-odd copy and the FP32 copy used by low-precision operators. */
+/* Load the gauge field U (Section 2: the links the action and the trajectory
+ * act on) from a lexicographic FP64 array (device, V * 72 doubles, read only);
+ * builds the FP64 even-odd copy and the FP32 copies used by low-precision
+ * operators. */
 int wd_gauge_load(wd_ctx* ctx, const double* U_lex);
+/* Write the context's current links to a lexicographic FP64 array (device,
+ * V * 72 doubles).  WD_ERR_STATE before any load. */
 int wd_gauge_store(wd_ctx* ctx, double* U_lex);
 
-/* Lexicographic spinor <-> half spinor of one parity (other parity ignored /
- * left untouched by unpack). */
+/* Lexicographic spinor <-> half spinor of one parity (Section 3.1, even-odd
+ * preconditioning splits fields by parity; the other parity is ignored by
+ * pack and left untouched by unpack).  WD_ERR_ARG unless parity is 0 or 1. */
 int wd_spinor_pack(wd_ctx* ctx, int parity, const double* lex, double* eo);
 int wd_spinor_unpack(wd_ctx* ctx, int parity, const double* eo, double* lex);
-/* Lexicographic algebra field <-> EO algebra field. */
+/* Lexicographic algebra field <-> EO algebra field (Section 2: momenta P and
+ * forces F live on the links, one su(3) element each). */
 int wd_algebra_pack(wd_ctx* ctx, const double* lex, double* eo);
 int wd_algebra_unpack(wd_ctx* ctx, const double* eo, double* lex);
 
 /* ---- operators (Section 3.1: Wilson, even-odd) ------------------------------ */
 
-/* out = D_{out_parity <- 1-out_parity} in (dagger: D^dag), half spinors.
- * prec selects the arithmetic: inputs are converted, outputs returned in FP64. */
+/* out = D_{out_parity <- 1-out_parity} in (dagger: D^dag), half spinors: the
+ * hopping term of the Wilson matrix M = 1 - kappa D (Section 3.1), one parity
+ * block of the even-odd split.  prec selects the arithmetic: inputs are
+ * converted, outputs returned in FP64.  in and out distinct; WD_ERR_STATE
+ * before a gauge load. */
 int wd_hop(wd_ctx* ctx, int out_parity, int dagger, int prec, const double* in, double* out);
-/* out = M_hat in or M_hat^dag in, M_hat = 1 - kappa^2 D_eo D_oe (even sites). */
+/* out = M_hat in or M_hat^dag in, M_hat = 1 - kappa^2 D_eo D_oe (even sites):
+ * the even-odd preconditioned Wilson matrix of Section 3.1, det M = det M_hat. */
 int wd_apply(wd_ctx* ctx, double kappa, int dagger, int prec, const double* in, double* out);
-/* out = K_hat in, K_hat = M_hat^dag M_hat; nrhs consecutive half spinors
- * (stride 24*Vh doubles).  One K_hat per right-hand side counts as N_mat. */
+/* out = K_hat in, K_hat = M_hat^dag M_hat (Section 2: K = M^dag M; Section 3.1:
+ * one multiplication by K is the unit N_mat of the cost); nrhs consecutive half
+ * spinors (stride 24*Vh doubles).  One K_hat per right-hand side counts as N_mat. */
 int mdagm_apply(wd_ctx* ctx, double kappa, int prec, int nrhs, const double* in, double* out);
 
 /* ---- solvers (Section 2: "iterative solvers (e.g. conjugate gradient)") ----- */
 
-/* Solve A x = b on even sites, A = K_hat(kappa), or A = K_hat P(K_hat) when
- * filt != NULL (filtered term).  x is the initial guess on entry.  Mixed
- * precision (p->prec != WD_F64) runs the bulk in that precision and
- * recomputes the residual in FP64 (reliable updates). */
+/* Solve A x = b on even sites, A = K_hat(kappa) (Section 2: K inverted by an
+ * iterative solver such as CG), or A = K_hat P(K_hat) when filt != NULL (the
+ * [P(K) K]^-1 of the filtered action S_PF, Section 2).  x is the initial guess
+ * on entry.  Mixed precision (p->prec != WD_F64) runs the bulk in that
+ * precision and recomputes the residual in FP64 (reliable updates).
+ * WD_ERR_NOCONV at maxiter, WD_ERR_NAN on a non-finite value. */
 int cg_solve(wd_ctx* ctx, double kappa, const wd_poly* filt, const double* b, double* x,
              const wd_cg_params* p, wd_cg_info* info);
-/* out = P(K_hat(kappa)) in by the Chebyshev three-term recurrence (n K_hat). */
+/* out = P(K_hat(kappa)) in, the polynomial filter P(K) ~ K^-1 of Section 2,
+ * by the Chebyshev three-term recurrence (n K_hat).  prec WD_F64 or WD_F32;
+ * in and out must differ. */
 int poly_filter_apply(wd_ctx* ctx, double kappa, const wd_poly* poly, int prec,
                       const double* in, double* out);
 
 /* ---- actions and forces (Section 2, eq. of the fermion force) --------------- */
 
-/* S of one term for the half spinor phi; *S is HOST memory. */
+/* S of one term for the half spinor phi (Section 2: S_F, the Hasenbusch and
+ * filtered terms of S_MP and S_PF; Section 4.1: S_PF-MP; Section 3.3: the
+ * ratio term of S_2PF); *S is HOST memory. */
 int pf_action(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
               double* S);
-/* phi such that S(phi) = chi^dag chi for a Gaussian half spinor chi. */
+/* phi such that S(phi) = chi^dag chi for a Gaussian half spinor chi (Section 2:
+ * the pseudofermions are drawn from exp(-S)).  chi and phi must differ. */
 int pf_heatbath(wd_ctx* ctx, const wd_term* term, const double* chi, const wd_cg_params* p,
                 double* phi);
-/* F += coef * dS/dw (algebra field).  Stores only X = A^-1 psi and Y = M_hat X
- * per term; polynomial intermediates are recomputed from checkpoints. */
+/* F += coef * dS/dw (algebra field): the fermion force of Section 2,
+ * -phi^dag K^-1 (dK/dU) K^-1 phi for the two-flavour term and its analogues for
+ * the other kinds.  Stores only X = A^-1 psi and Y = M_hat X per term;
+ * polynomial intermediates are recomputed from checkpoints. */
 int fermion_force(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_cg_params* p,
                   double coef, double* F);
 /* pf_action that also returns the vectors the force needs (differentiation
@@ -211,25 +241,32 @@ int pf_action_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const wd_c
  * X); POLY and RATIO need neither.  prec: WD_F64 or WD_F32 arithmetic. */
 int fermion_force_xy(wd_ctx* ctx, const wd_term* term, const double* phi, const double* X,
                      const double* Y, int prec, double coef, double* F);
-/* Wilson plaquette action S_G = beta sum (1 - Re tr U_p / 3); *S host. */
+/* Gauge action S_G of Section 2 (named there only; reading: the Wilson plaquette
+ * action S_G = beta sum_{x, mu<nu} (1 - Re tr U_p / 3)); *S host. */
 int gauge_action(wd_ctx* ctx, double beta, double* S);
-/* F += coef * dS_G/dw. */
+/* F += coef * dS_G/dw, the gauge part of the force F = dS/dU of Section 2
+ * (staple sum per link); prec WD_F64 or WD_F32. */
 int gauge_force(wd_ctx* ctx, double beta, int prec, double coef, double* F);
 
 /* ---- HMC steps (Section 2, eqs. for T-hat and S-hat) ------------------------ */
 
-/* U <- exp(i eps P) U on every link, reunitarised, FP64. */
+/* T[eps] of Section 2: U <- exp(i eps P) U on every link, reunitarised, FP64;
+ * refreshes the low-precision link copies. */
 int step_T(wd_ctx* ctx, const double* P, double eps);
-/* P <- P - eps F. */
+/* S[eps] of Section 2: P <- P - eps F (algebra fields, FP64). */
 int step_S(wd_ctx* ctx, double* P, const double* F, double eps);
-/* sum tr P^2 = (1/2) sum_a P_a^2, FP64; *out host. */
+/* The kinetic term of H = sum tr P^2 + S (Section 2): sum tr P^2 =
+ * (1/2) sum_a P_a^2, FP64; *out host. */
 int kinetic_energy(wd_ctx* ctx, const double* P, double* out);
-/* Gaussian draws by Philox4x64-10 (key (seed,0), counter (j, stream, 0, 0)):
+/* Gaussian draws for the momenta and the pseudofermion noise (Section 2: P and
+ * chi Gaussian distributed) by Philox4x64-10 (Salmon et al. 2011; key (seed,0),
+ * counter (j, stream, 0, 0)):
  * what = 0: half spinor of parity `parity` with N(0,1) real and imaginary parts
  *           (lexicographic element order decides the draw);
  * what = 1: algebra field (momenta), N(0,1) per coordinate. */
 int gaussian_draw(wd_ctx* ctx, int what, int parity, uint64_t seed, uint64_t stream, double* out);
-/* Accept iff u < exp(-dH); host-only, no device work. */
+/* The Metropolis test of Section 2: accept iff u < exp(-dH), u in [0, 1) (else
+ * WD_ERR_ARG); host-only, no device work. */
 int metropolis(double dH, double u, int* accept);
 
 /* Cost of an action over n trajectories (Section 3.1, the cost metric):
@@ -248,8 +285,9 @@ int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n
 
 /* ---- HMC trajectory ---------------------------------------------------------- */
 
-/* One operation of an integrator: kind 0 = T[eps]; kind 1 = S[eps] for the
- * terms in group `group` (group -1 = gauge action). */
+/* One operation of an integrator (Section 2: T[eps] and S[eps]; Section 3.2:
+ * one time scale per group): kind 0 = T[eps]; kind 1 = S[eps] for the terms in
+ * group `group` (group -1 = gauge action). */
 typedef struct { int kind; int group; double eps; } wd_op;
 
 typedef struct {
@@ -283,7 +321,8 @@ typedef struct {
   double t_force_group_ms[4];
 } wd_hmc_result;
 
-/* Heat bath, momentum draw, integration, accept/reject with uniform u (host).
+/* One HMC trajectory (Section 2): heat bath, momentum draw, integration,
+ * accept/reject with uniform u (host).
  * Draws: momenta P_a ~ N(0,1) per coordinate (density exp(-sum tr P^2)) from
  * Philox stream 64 traj_index; the noise of term i is chi ~ exp(-chi^dag chi)
  * (Section 2: real and imaginary parts N(0, 1/2)), the stream 64 traj_index
@@ -347,13 +386,18 @@ int wd_schedule_generalised(int kind, double tau, int ngroups, const int* groups
  * once for all of them, and one launch covers every lattice.  Allocates its
  * fields (6 FP32 vectors per lattice and rhs) at creation. */
 typedef struct wd_batch wd_batch;
+/* Group nlat contexts (host array) with kappas[l] and nrhs[l] in 1..8 (host
+ * arrays) into one batch (Section 2: several pseudofermion solves with K).
+ * WD_ERR_ARG on mixed streams, a context without links or nrhs out of range. */
 int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const int* nrhs, wd_batch** out);
+/* Free the batch's fields (not the contexts).  NULL is accepted. */
 int wd_batch_destroy(wd_batch* b);
-/* out[l] = K_hat in[l] per system, FP32 with FP32 links of the contexts'
+/* out[l] = K_hat in[l] per system (Section 2: K = M^dag M), FP32 with FP32 links of the contexts'
  * storage (12 or 18 reals, from the first context).  in[l], out[l]: nrhs[l]
  * consecutive FP64 half spinors of lattice l (device). */
 int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
-/* Mixed-precision CG for every system from x = 0: FP32 batched iterations,
+/* CG (Section 2: the iterative solver of K) for every system from x = 0,
+ * mixed precision: FP32 batched iterations,
  * FP64 reliable updates per system (through its context) to the FP64 true
  * residual p->tol.  p->check_every iterations (default 16) run between host
  * checks, as one captured CUDA graph when use_graph (systems that have
@@ -362,7 +406,8 @@ int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
  * the batched kernels on K_hat b and keeps the fastest. */
 int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const wd_cg_params* p, int use_graph,
                 wd_cg_info* infos);
-/* Systems, block size chosen by the tuner, kernels launched so far. */
+/* Systems, block size chosen by the tuner, kernels launched so far (no
+ * counterpart in the paper). */
 int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches);
 
 /* ---- allocation-free K_hat ----------------------------------------------------
@@ -386,15 +431,19 @@ int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches
  * Every call shares that array and overwrites it; calls that overlap on the
  * GPU race on it and must be serialised by the caller.  The first call on a
  * device looks up the array's address with that device current; make that
- * first call before any stream capture. */
+ * first call before any stream capture.  That address is kept per device for
+ * the life of the process and belongs to the device's primary context: after
+ * cudaDeviceReset, or under another driver-API context, do not call this. */
 int mdagm_apply_noalloc(const int dims[4], const double* gauge_eo, double kappa, const double* in,
                         double* out, void* stream);
 
 /* ---- counters and timing ---------------------------------------------------- */
 
-/* N_mat: K_hat applications since the context was created or reset. */
+/* N_mat (Section 3.1: the multiplications by K that the cost counts): K_hat
+ * applications since the context was created or reset. */
 int wd_nmat(wd_ctx* ctx, long long* count, int reset);
-/* Sample every n-th launch of the hop kernels with CUDA events on the context
+/* Measurement, no counterpart in the paper.  Sample every n-th launch of the
+ * hop kernels with CUDA events on the context
  * stream (n = 0 disables; launches queued inside a CG chunk, which may return
  * early after convergence, are not sampled).  wd_profile_read gives, for the
  * hop kernels whose input spinors have format fmt (enum wd_prec, or -1 for
@@ -403,10 +452,11 @@ int wd_nmat(wd_ctx* ctx, long long* count, int reset);
  * moved once). */
 int wd_profile_enable(wd_ctx* ctx, int every_n);
 int wd_profile_read(wd_ctx* ctx, int fmt, long long* launches, double* total_ms, double* bytes);
-/* Kernels launched by this context since it was created. */
+/* Kernels launched by this context since it was created (no counterpart in
+ * the paper). */
 int wd_launch_count(wd_ctx* ctx, long long* count);
 /* Hop launches per input format (FP64, FP32, FP16, BF16, double-float) since
- * the last wd_profile_enable, sampled or not. */
+ * the last wd_profile_enable, sampled or not (no counterpart in the paper). */
 int wd_hop_counts(wd_ctx* ctx, long long counts[5]);
 
 #ifdef __cplusplus

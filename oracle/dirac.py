@@ -4,7 +4,7 @@ The paper (Section 3.1) uses Wilson fermions without fixing a spinor basis.
 Reading: the chiral DeGrand-Rossi basis, gamma_5 = gamma_1 gamma_2 gamma_3
 gamma_4.  Every quantity the tests compare (spectra, actions, forces) is
 basis independent; the CUDA path states the same basis on its own.
-Pinned by tests/test_oracle_dirac.py (Clifford algebra, hermiticity,
+Pinned by tests/test_oracle_wilson.py (Clifford algebra, hermiticity,
 gamma_5 = diag(1,1,-1,-1)).
 """
 import numpy as np

@@ -17,7 +17,7 @@ Field-draw convention (shared by definition, not by code, with the CUDA path):
      g0 = sqrt(-2 ln u0) cos(2 pi u1),  g1 = sqrt(-2 ln u0) sin(2 pi u1),
      g2 = sqrt(-2 ln u2) cos(2 pi u3),  g3 = sqrt(-2 ln u2) sin(2 pi u3).
 
-Pinned against numpy's own Philox bit generator (tests/test_oracle_rng.py).
+Pinned against numpy's own Philox bit generator (tests/test_oracle_algebra.py).
 Only tests/, bench.py's CPU-baseline leg and the smoke check may import this.
 """
 import numpy as np

@@ -20,7 +20,11 @@
 //     the caller;
 //   - on its first call on a device the entry point looks up the array's
 //     device address (cudaGetSymbolAddress) with that device current; make
-//     that first call before any stream capture.
+//     that first call before any stream capture.  The address is kept per
+//     device index for the life of the process, so it belongs to the device's
+//     primary context: after cudaDeviceReset, or under a driver-API context
+//     other than the primary one, it no longer names the array and the entry
+//     point must not be used.
 #include <mutex>
 
 #include "dslash_impl.cuh"

@@ -168,6 +168,19 @@ struct SpF32 {
       p[j * stride + i] = make_float4((float)s[2 * j].r, (float)s[2 * j].i, (float)s[2 * j + 1].r,
                                       (float)s[2 * j + 1].i);
   }
+  // the stored words of one site, loaded ahead of their use
+  struct Raw { float4 v[6]; };
+  __device__ __forceinline__ void loadRaw(long i, Raw& r) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) r.v[j] = __ldg(p + j * stride + i);
+  }
+  template <class T> __device__ __forceinline__ static void unpack(const Raw& r, cpx<T> (&s)[12]) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      s[2 * j] = {(T)r.v[j].x, (T)r.v[j].y};
+      s[2 * j + 1] = {(T)r.v[j].z, (T)r.v[j].w};
+    }
+  }
 };
 
 template <class H> struct H16Traits;
@@ -217,6 +230,24 @@ template <class H> struct Sp16 {
         w[q] = lo | (hi << 16);
       }
       p[j * stride + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  // the stored words of one site (16-bit values and the norm), loaded ahead of their use
+  struct Raw { uint4 v[3]; float n; };
+  __device__ __forceinline__ void loadRaw(long i, Raw& r) const {
+    r.n = __ldg(nrm + i);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.v[j] = __ldg(p + j * stride + i);
+  }
+  template <class T> __device__ __forceinline__ static void unpack(const Raw& r, cpx<T> (&s)[12]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      unsigned w[4] = {r.v[j].x, r.v[j].y, r.v[j].z, r.v[j].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s[4 * j + q] = {(T)(r.n * H16Traits<H>::to_f((unsigned short)(w[q] & 0xffffu))),
+                        (T)(r.n * H16Traits<H>::to_f((unsigned short)(w[q] >> 16)))};
+      }
     }
   }
 };

@@ -6,8 +6,9 @@ device memory belongs to another pool manager, or they cannot afford the
 synchronisation of cudaMalloc, or must not fail on allocation): its scratch
 is a fixed static device array.  Checked here through the C ABI: two calls in
 a row on different inputs each match mdagm_apply to the FP64 tolerance of
-the operator tests (1e-12 per site), and a lattice beyond the fixed scratch
-size is rejected before any launch.  Collected last on purpose.
+the operator tests (1e-12 per site), so does a call with in and out the same
+buffer, and a lattice beyond the fixed scratch size or with an odd, zero or
+negative extent is rejected before any launch.  Collected last on purpose.
 """
 import ctypes as C
 
@@ -57,6 +58,13 @@ def test_noalloc_matches_mdagm_apply(dims):
         torch.cuda.synchronize()
         err = gu.site_rel_err(gu.unpack(lat, out, 0), gu.unpack(lat, ref, 0), 0, dims)
         assert err < 1e-12, (call, err)
+    # in and out may be the same buffer: out is written only by the last launch
+    io = x.clone()
+    rc = wd.lib.mdagm_apply_noalloc(d, C.c_void_p(G.data_ptr()), kappa, C.c_void_p(io.data_ptr()),
+                                    C.c_void_p(io.data_ptr()), stream)
+    assert rc == 0, wd.lib.wd_last_error().decode()
+    torch.cuda.synchronize()
+    assert gu.site_rel_err(gu.unpack(lat, io, 0), gu.unpack(lat, ref, 0), 0, dims) < 1e-12
     lat.close()
 
 
@@ -69,3 +77,19 @@ def test_noalloc_rejects_oversized_lattice():
     rc = wd.lib.mdagm_apply_noalloc(d, p, 0.12, p, p, None)
     assert rc == 1
     assert "32768" in wd.lib.wd_last_error().decode()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 5), (4, 0, 4, 4), (3, 4, 4, 4), (4, 4, -2, 4)],
+                         ids=["odd_t", "zero", "odd_x", "negative"])
+def test_noalloc_rejects_bad_extents(dims):
+    """Odd, zero or negative extents are rejected with WD_ERR_ARG before any work."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    d = (C.c_int * 4)(*dims)
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    p = C.c_void_p(buf.data_ptr())
+    rc = wd.lib.mdagm_apply_noalloc(d, p, 0.12, p, p, None)
+    assert rc == 1
+    assert "even" in wd.lib.wd_last_error().decode()
+    torch.cuda.synchronize()
+    assert float(buf.abs().sum()) == 0.0
