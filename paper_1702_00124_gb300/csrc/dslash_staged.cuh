@@ -26,6 +26,11 @@ namespace wd {
 #ifndef WD_HOP_MINB
 #define WD_HOP_MINB 5
 #endif
+// L2 prefetch size of the stencil's global reads: 0 none, 1 the link copies
+// fetch 256-byte L2 lines, 2 the neighbour spinor reads as well
+#ifndef WD_HOP_L2_256
+#define WD_HOP_L2_256 0
+#endif
 constexpr int HOP_NST = WD_HOP_STAGES;                 // link directions in flight
 // neighbour spinor of direction D + 1 loaded into registers while D is computed
 constexpr bool HOP_SPIN_AHEAD = WD_HOP_SPIN_AHEAD != 0;
@@ -36,7 +41,38 @@ constexpr size_t HOP_STAGE_SMEM = (size_t)(HOP_NST + 1) * 3 * HOP_ST_THREADS * s
 
 __device__ __forceinline__ void cpa16(float4* sdst, const float4* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+#if WD_HOP_L2_256 >= 1
+  asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+#else
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+#endif
+}
+
+// read-only 16-byte load with the L2 prefetch size of WD_HOP_L2_256 >= 2
+__device__ __forceinline__ float4 ldg_stencil(const float4* p) {
+#if WD_HOP_L2_256 >= 2
+  float4 v;
+  asm volatile("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+
+// neighbour spinor of the staged stencil: FP32 through ldg_stencil, other
+// formats through their own loader
+template <class S> __device__ __forceinline__ void load_nbr(const S& in, long i, cpx<float> (&s)[12]) {
+  in.loadT(i, s);
+}
+template <> __device__ __forceinline__ void load_nbr<SpF32>(const SpF32& in, long i, cpx<float> (&s)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float4 v = ldg_stencil(in.p + j * in.stride + i);
+    s[2 * j] = {v.x, v.y};
+    s[2 * j + 1] = {v.z, v.w};
+  }
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cpa_wait() {
@@ -76,7 +112,7 @@ struct Staged {
 
   template <int D> __device__ __forceinline__ void step(cpx<float> (&acc)[12]) const {
     cpx<float> s[12];
-    a.in.loadT(nbr<D>(), s);
+    load_nbr(a.in, nbr<D>(), s);
     compute<D>(acc, s);
   }
 
