@@ -627,6 +627,8 @@ def main():
                                               "poly_f32_recon12"],
                     help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
     ap.add_argument("--reps", type=int, default=4)
+    ap.add_argument("--n-outer", type=int, default=None,
+                    help="outer integrator steps (default: the workload's; fewer only for short ncu launch lists)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -660,7 +662,8 @@ def main():
     terms = [wd.term(wd.POLY, w["kappa_h"], poly=w["poly"]), wd.term(wd.FILTERED, w["kappa_h"], poly=w["poly"]),
              wd.term(wd.HASENBUSCH, w["kappa"], w["kappa_h"])]
     groups = [1, 0, 0]
-    ops = wd.wd_schedule_nested(1, w["tau"], [g for g, _ in LEVELS], [n for _, n in LEVELS])
+    levels = [(g, (args.n_outer or w["n_outer"]) if g == 0 else n) for g, n in LEVELS]
+    ops = wd.wd_schedule_nested(1, w["tau"], [g for g, _ in levels], [n for _, n in levels])
     cg_md = wd.cg_params(tol=1e-10, prec=wd.F32, maxiter=20000)
     cg_acc = wd.cg_params(tol=1e-10, prec=wd.F32, maxiter=20000)
     traj = [0]
@@ -748,7 +751,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "dims": list(dims), "kappa": w["kappa"],
                            "kappa_h": w["kappa_h"], "poly": list(w["poly"]), "beta": w["beta"],
-                           "integrator": "nested Omelyan 2MN", "levels": LEVELS, "tau": w["tau"],
+                           "integrator": "nested Omelyan 2MN", "levels": levels, "tau": w["tau"],
                            "action": "PF-MP + Wilson gauge",
                            "precision": "FP32 bulk (12-real links); reliable updates with b, x, r, dots in FP64 and "
                                         + ("A x in double-float (2xFP32, ~48 bits)" if RESIDUAL_MODE else "A x in FP64")

@@ -21,10 +21,18 @@ namespace wd {
 #define WD_HOP_STAGES 2
 #endif
 #ifndef WD_HOP_SPIN_AHEAD
-#define WD_HOP_SPIN_AHEAD 0
+#define WD_HOP_SPIN_AHEAD 1
 #endif
-#ifndef WD_HOP_MINB
-#define WD_HOP_MINB 5
+// resident 128-thread blocks per SM the register budget is set for: FP32
+// spinors five (96 registers), 16-bit spinors six (80 registers; their words
+// take half the registers).  Measured per hop at 32^3 x 64 in the K_hat chain:
+// FP32 0.1112 ms (five, with the look-ahead below) against 0.1163 (six) and
+// 0.1283 (seven); BF16 0.1070 ms (six) against 0.1104 (five).
+#ifndef WD_HOP_MINB_F32
+#define WD_HOP_MINB_F32 5
+#endif
+#ifndef WD_HOP_MINB_16
+#define WD_HOP_MINB_16 6
 #endif
 // L2 prefetch size of the stencil's global reads: 0 none, 1 the link copies
 // fetch 256-byte L2 lines, 2 the neighbour spinor reads as well
@@ -32,9 +40,16 @@ namespace wd {
 #define WD_HOP_L2_256 0
 #endif
 constexpr int HOP_NST = WD_HOP_STAGES;                 // link directions in flight
-// neighbour spinor of direction D + 1 loaded into registers while D is computed
-constexpr bool HOP_SPIN_AHEAD = WD_HOP_SPIN_AHEAD != 0;
-constexpr int HOP_MINB = WD_HOP_MINB;                  // resident blocks per SM the registers allow
+// neighbour spinor of direction D + 1 loaded into registers while D is computed:
+// 0 never, 1 for FP32 spinors (0.1133 -> 0.1112 ms per hop; 16-bit spinors gain
+// nothing), 2 for every format
+template <class In> constexpr bool spin_ahead() {
+  return WD_HOP_SPIN_AHEAD >= 2 || (WD_HOP_SPIN_AHEAD == 1 && std::is_same<In, SpF32>::value);
+}
+template <class In> constexpr int hop_minb() {
+  return std::is_same<In, SpF32>::value ? WD_HOP_MINB_F32 : WD_HOP_MINB_16;
+}
+constexpr int HOP_MINB = WD_HOP_MINB_F32;              // FP32 kernels outside the template
 static_assert(HOP_NST >= 1 && HOP_NST <= 7, "one to seven directions in flight");
 constexpr int HOP_ST_THREADS = 128;
 constexpr size_t HOP_STAGE_SMEM = (size_t)(HOP_NST + 1) * 3 * HOP_ST_THREADS * sizeof(float4);
@@ -163,8 +178,9 @@ struct Staged {
 
   __device__ __forceinline__ void run(cpx<float> (&acc)[12]) const {
     prologue<0>();
-    if constexpr (HOP_SPIN_AHEAD) {
-      typename std::remove_cv<decltype(a.in)>::type::Raw r0, r1;
+    using In = typename std::remove_cv<decltype(a.in)>::type;
+    if constexpr (spin_ahead<In>()) {
+      typename In::Raw r0, r1;
       a.in.loadRaw(nbr<0>(), r0);
       step_ahead<0>(acc, r0, r1);
       step_ahead<1>(acc, r1, r0);
@@ -188,7 +204,7 @@ struct Staged {
 };
 
 template <bool DAG, bool XPAY, bool NORM, class In, class Out, class Y>
-__global__ void __launch_bounds__(HOP_ST_THREADS, HOP_MINB) k_hop_st(HopArgs<In, Out, Y, GF32R12> a) {
+__global__ void __launch_bounds__(HOP_ST_THREADS, hop_minb<In>()) k_hop_st(HopArgs<In, Out, Y, GF32R12> a) {
   extern __shared__ float4 sbuf[];
   if (a.st != nullptr && a.st->flag != 0) return;
   const long cb = (long)blockIdx.x * blockDim.x + threadIdx.x;
