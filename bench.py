@@ -45,6 +45,7 @@ WORKLOADS = {
                            poly=(24, 0.005, 8.0), beta=5.6, tau=1.0, n_outer=10),
 }
 DEFAULT_WORKLOAD = "c5_32x32x32x64"
+STENCILS = {"thread": 0, "tile": 1}
 # Integrator levels, outermost first: (group, steps per enclosing T).
 # group 0: filtered + Hasenbusch terms, group 1: P(J) term, -1: gauge action.
 LEVELS = [(0, 10), (1, 1), (-1, 2)]
@@ -374,16 +375,35 @@ def kernel_case(args):
                    "khat_f64": (wd.F64, 0), "khat_df": (wd.DF, 0),
                    "poly_f32_recon12": (wd.F32, 1)}[args.kernel_case]
     lat.wd_set_recon(recon)
+    lat.wd_set_stencil(STENCILS[args.stencil])
+    if args.profile:
+        lat.wd_profile_enable(1)   # every hop launch bracketed by CUDA events (not under ncu)
     x, y = lat.half_spinor(), lat.half_spinor()
     lat.gaussian_draw(0, 0, 1, 1, x)
+    stream = torch.cuda.current_stream()
+    ms = []
     for _ in range(args.reps):
+        # K_hat chain: each application reads what the previous one wrote, as in CG
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         if args.kernel_case.startswith("poly"):
             lat.poly_filter_apply(w["kappa_h"], (4, w["poly"][1], w["poly"][2]), prec, x, y)
         else:
             lat.mdagm_apply(w["kappa"], prec, 1, x, y)
+        e1.record(stream)
+        x, y = y, x
+        ms.append((e0, e1))
     torch.cuda.synchronize()
+    t = sorted(a.elapsed_time(b) for a, b in ms[min(3, len(ms) - 1):])
+    status = lat.wd_kernel_status()
+    hops = lat.wd_profile_read(prec if prec != wd.DF else 4)
     lat.close()
-    print(f"kernel case {args.kernel_case} on {args.workload}: {args.reps} K_hat applications")
+    n_khat = 4 if args.kernel_case.startswith("poly") else 1
+    hop = (f"; sampled hops (plain, xpay, dagger): {hops['launches']} launches, "
+           f"{hops['ms'] / max(hops['launches'], 1):.4f} ms each, "
+           f"{hops['bytes'] / max(hops['ms'], 1e-9) / 1e6:.0f} GB/s algorithmic") if args.profile else ""
+    print(f"kernel case {args.kernel_case} on {args.workload} ({args.stencil} stencil): {args.reps} calls of "
+          f"{n_khat} K_hat; median {t[len(t) // 2]:.4f} ms per call{hop}; kernel status {status}")
 
 
 def e2e_run(lat, w, terms, groups, ops, cg_md, cg_acc, force_prec, seed, traj, n=2):
@@ -627,6 +647,10 @@ def main():
                                               "poly_f32_recon12"],
                     help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
     ap.add_argument("--reps", type=int, default=4)
+    ap.add_argument("--profile", action="store_true", help="kernel case: time every hop with CUDA events")
+    ap.add_argument("--stencil", default="thread", choices=sorted(STENCILS),
+                    help="kernel case: 12-real-link stencil kernel (thread: per-thread staging, the default; "
+                         "tile: tile-staged bulk copies)")
     ap.add_argument("--n-outer", type=int, default=None,
                     help="outer integrator steps (default: the workload's; fewer only for short ncu launch lists)")
     args = ap.parse_args()

@@ -111,10 +111,13 @@ int wd_context_create(const int dims[4], void* stream, wd_ctx** out) {
   al((void**)&c->red_counter, sizeof(unsigned) * 4);
   al((void**)&c->red_out, sizeof(double) * 16);
   al((void**)&c->cgs, sizeof(CGState));
+  al((void**)&c->kerr, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->cgs_host, sizeof(CGState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_scalar, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, sizeof(unsigned) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->cgs, 0, sizeof(CGState));
+  if (e == cudaSuccess) e = cudaMemset(c->kerr, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
     std::string m = std::string("wd_context_create: ") + cudaGetErrorString(e);
     wd_context_destroy(c);
@@ -136,6 +139,7 @@ int wd_context_destroy(wd_ctx* c) {
   cudaFree(c->red_counter);
   cudaFree(c->red_out);
   cudaFree(c->cgs);
+  cudaFree(c->kerr);
   cudaFree(c->gauge_backup);
   cudaFree(c->mom);
   cudaFree(c->lex_stage);
@@ -184,6 +188,27 @@ int wd_set_residual(wd_ctx* c, int mode) {
   if (mode == 1) WD_TRY(ensure_gauge_dd(c));
   c->resid_dd = mode;
   return WD_OK;
+}
+
+int wd_set_stencil(wd_ctx* c, int stencil) {
+  CHECK_CTX(c);
+  if (stencil != WD_STENCIL_THREAD && stencil != WD_STENCIL_TILE)
+    return fail(WD_ERR_ARG, "stencil must be WD_STENCIL_THREAD (0) or WD_STENCIL_TILE (1)");
+  c->stencil = stencil;
+  return WD_OK;
+}
+
+int wd_kernel_status(wd_ctx* c, unsigned* word) {
+  CHECK_CTX(c);
+  unsigned* h = (unsigned*)c->host_scalar;
+  WD_CUDA(cudaMemcpyAsync(h, c->kerr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  const unsigned w = *h;
+  if (word) *word = w;
+  if (w == 0) return WD_OK;
+  WD_CUDA(cudaMemsetAsync(c->kerr, 0, sizeof(unsigned), c->stream));
+  WD_CUDA(cudaStreamSynchronize(c->stream));
+  return fail(WD_ERR_TIMEOUT, "a bounded device-side wait expired in a stencil kernel");
 }
 
 int wd_volume(const wd_ctx* c, long long out[2]) {

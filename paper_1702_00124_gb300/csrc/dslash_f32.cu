@@ -1,6 +1,6 @@
 // FP32 instantiations of the hopping stencil (float storage and arithmetic,
 // FP32 links with 18 or 12 stored reals).
-#include "dslash_staged.cuh"
+#include "dslash_tt.cuh"
 
 namespace wd {
 
@@ -9,7 +9,10 @@ int hop_f32(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out,
   if (in.fmt != WD_F32 || out.fmt != WD_F32 || (y && y->fmt != WD_F32))
     return fail(WD_ERR_ARG, "hop_f32: field formats must all be FP32");
   SpF32 I = sp32(in), O = sp32(out), Y = y ? sp32(*y) : O;
-  if (c->recon == WD_RECON_12) return hop_staged(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg);
+  if (c->recon == WD_RECON_12) {
+    if (tt_eligible(c)) return hop_tt(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg);
+    return hop_staged(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg);
+  }
   return hop_with_gauge<float>(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg, false);
 }
 
@@ -85,17 +88,26 @@ int khat_poly_step_f32(wd_ctx* c, double kappa, const Field& s, Field& t1, Field
   WD_TRY(hop(c, 0, false, t1, t2, &s, a2, false, false));
   WD_TRY(hop(c, 1, true, t2, t1, nullptr, 0.0, false, false));
   const int nb = nblocks(c->g.Vh, 128);
-  if (c->recon == WD_RECON_12) {
+  if (c->recon == WD_RECON_12 && tt_eligible(c)) {
+    HopArgs<SpF32, SpF32, SpF32, GF32R12> a{c->g, 0, sp32(t1), sp32(out), sp32(t2), GF32R12{c->gauge32r12, c->g.Vh},
+                                            a2, reducer(c), nullptr};
+    const TTPoly pe{sp32(v), sp32(s), sp32(sprev), (float)ca, (float)cmu, (float)cb};
+    const Field* chk[] = {&t1, &t2, &v, &s, &sprev};
+    for (const Field* f : chk)
+      if (((uintptr_t)f->data & 15) != 0) return fail(WD_ERR_ARG, "khat_poly_step_f32: fields must be 16-byte aligned");
+    WD_TRY((tt_launch<true, 2, false>(c, a, pe)));
+  } else if (c->recon == WD_RECON_12) {
     HopArgs<SpF32, SpF32, SpF32, GF32R12> a{c->g, 0, sp32(t1), sp32(out), sp32(t2), GF32R12{c->gauge32r12, c->g.Vh},
                                             a2, reducer(c), nullptr};
     k_hop_poly_st<<<nb, HOP_ST_THREADS, HOP_STAGE_SMEM, c->stream>>>(a, sp32(v), sp32(s), sp32(sprev), (float)ca,
                                                                       (float)cmu, (float)cb);
+    WD_CHECK_LAUNCH();
   } else {
     HopArgs<SpF32, SpF32, SpF32, GF32> a{c->g, 0, sp32(t1), sp32(out), sp32(t2), GF32{c->gauge32, c->g.Vh}, a2,
                                          reducer(c), nullptr};
     k_hop_poly<<<nb, 128, 0, c->stream>>>(a, sp32(v), sp32(s), sp32(sprev), (float)ca, (float)cmu, (float)cb);
+    WD_CHECK_LAUNCH();
   }
-  WD_CHECK_LAUNCH();
   c->prof.all[WD_F32] += 1;
   c->nmat += 1;
   return WD_OK;

@@ -315,6 +315,7 @@ static int cg_core(wd_ctx* c, const Op& op, const Field& b, const Field& x, cons
         WD_TRY(cg_pupdate(c, rs, ps));
       }
       WD_TRY(download_state(c));
+      if (st.flag & FLAG_TIMEOUT) { status = fail(WD_ERR_TIMEOUT, "cg: a bounded stencil wait expired"); break; }
       if (st.flag & FLAG_NAN) { status = fail(WD_ERR_NAN, "cg: non-finite value in the iteration"); break; }
       if (st.flag == 0) continue;
       // fold the sloppy increment into x and recompute the FP64 residual

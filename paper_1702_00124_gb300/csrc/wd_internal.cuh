@@ -409,7 +409,7 @@ __device__ __forceinline__ bool grid_sum(const Reduce& r, double (&v)[NV], doubl
 // ----------------------------------------------------------------------------
 // Solver state kept on the device so that iterations can be queued without
 // host round trips.  Kernels return at once when flag != 0.
-enum : int { FLAG_DONE = 1, FLAG_UPDATE = 2, FLAG_NAN = 4, FLAG_MAXITER = 8 };
+enum : int { FLAG_DONE = 1, FLAG_UPDATE = 2, FLAG_NAN = 4, FLAG_MAXITER = 8, FLAG_TIMEOUT = 16 };
 struct CGState {
   double rr;        // |r|^2 of the current residual
   double rr_old;    // |r|^2 one iteration earlier
@@ -484,6 +484,9 @@ struct wd_ctx {
   long long nmat = 0;
   long long launches = 0;           // kernels launched by the library
   int autotune = 1;                 // time launch shapes on first use
+  int stencil = WD_STENCIL_THREAD;  // 12-real-link stencil: per-thread staging or tile-staged bulk copies
+  int nsm = 0;                      // multiprocessors of the device
+  unsigned* kerr = nullptr;         // device error word: bit 0 = a bounded wait expired
   std::unordered_map<long long, std::pair<int, int>> tune;   // key -> (threads, minb)
   std::unordered_map<long long, wd::TuneSamples> tune_samples;   // keys being tuned
   wd::Prof prof;

@@ -19,8 +19,10 @@ lib = C.CDLL(_LIB_PATH)
 
 F64, F32, F16, BF16, DF = 0, 1, 2, 3, 4   # DF: double-float (operator calls only)
 RECON_18, RECON_12 = 0, 1
+STENCIL_THREAD, STENCIL_TILE = 0, 1
 PLAIN, HASENBUSCH, POLY, FILTERED, RATIO = 0, 1, 2, 3, 4
-ERRORS = {1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_NOCONV", 4: "WD_ERR_NAN", 5: "WD_ERR_STATE"}
+ERRORS = {1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_NOCONV", 4: "WD_ERR_NAN", 5: "WD_ERR_STATE",
+          6: "WD_ERR_TIMEOUT"}
 
 
 class WdError(RuntimeError):
@@ -123,6 +125,8 @@ _SIG = {
     "pf_action_xy": ([_P, C.POINTER(wd_term), _P, C.POINTER(wd_cg_params), C.POINTER(_D), _P, _P], _I),
     "fermion_force_xy": ([_P, C.POINTER(wd_term), _P, _P, _P, _I, _D, _P], _I),
     "wd_set_residual": ([_P, _I], _I),
+    "wd_set_stencil": ([_P, _I], _I),
+    "wd_kernel_status": ([_P, C.POINTER(C.c_uint)], _I),
     "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
     "wd_tune_entry": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I)], _I),
     "wd_hop_counts": ([_P, C.POINTER(C.c_longlong)], _I),
@@ -311,6 +315,14 @@ class Lattice:
 
     def wd_set_residual(self, mode):
         _check(lib.wd_set_residual(self.h, mode))
+
+    def wd_set_stencil(self, stencil):
+        _check(lib.wd_set_stencil(self.h, stencil))
+
+    def wd_kernel_status(self):
+        w = C.c_uint(0)
+        _check(lib.wd_kernel_status(self.h, C.byref(w)))
+        return w.value
 
     def wd_set_autotune(self, enable=-1):
         n = C.c_int(0)
