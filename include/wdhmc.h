@@ -172,6 +172,14 @@ int wd_set_stencil(wd_ctx* ctx, int stencil);
  * WD_ERR_TIMEOUT if it was set, else WD_OK.  Solvers report an expiry inside
  * their iterations as WD_ERR_TIMEOUT themselves. */
 int wd_kernel_status(wd_ctx* ctx, unsigned* word);
+/* Self-test of the bounded device-side wait (no counterpart in the paper):
+ * launches one block on the context's stream whose first thread waits on a
+ * shared-memory barrier that nothing arrives at, with the bound timeout_ns
+ * (1e6 .. 1e10 ns) in place of the stencil's two seconds.  The wait expires,
+ * the kernel records it in the device error word and ends, so a following
+ * wd_kernel_status returns WD_ERR_TIMEOUT (and clears the word).  Nothing else
+ * of the context changes.  WD_ERR_ARG for a bound outside the range. */
+int wd_selftest_wait_timeout(wd_ctx* ctx, long long timeout_ns);
 /* Launch-shape autotuner of the hop kernels (no counterpart in the paper; on
  * by default): the first launch
  * of each (formats, link storage, dagger, epilogue) outside a queued CG chunk

@@ -211,6 +211,13 @@ int wd_kernel_status(wd_ctx* c, unsigned* word) {
   return fail(WD_ERR_TIMEOUT, "a bounded device-side wait expired in a stencil kernel");
 }
 
+int wd_selftest_wait_timeout(wd_ctx* c, long long timeout_ns) {
+  CHECK_CTX(c);
+  if (timeout_ns < 1000000LL || timeout_ns > 10000000000LL)
+    return fail(WD_ERR_ARG, "timeout_ns must lie in [1e6, 1e10]");
+  return wait_selftest(c, timeout_ns);
+}
+
 int wd_volume(const wd_ctx* c, long long out[2]) {
   CHECK_CTX(c);
   CHECK_PTR(out);

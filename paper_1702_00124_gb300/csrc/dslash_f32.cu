@@ -16,6 +16,26 @@ int hop_f32(wd_ctx* c, int out_par, bool dag, const Field& in, const Field& out,
   return hop_with_gauge<float>(c, out_par, dag, I, O, Y, y != nullptr, alpha, norm_cg, in_cg, false);
 }
 
+// Self-test of the bounded barrier wait: thread 0 waits on a freshly
+// initialised mbarrier that nothing arrives at; the wait expires after ns and
+// the kernel records it in the device error word and returns.
+__global__ void k_wait_selftest(unsigned* kerr, long long ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_ns(&bar, 0u, ns)) atomicOr(kerr, 1u);
+}
+
+int wait_selftest(wd_ctx* c, long long ns) {
+  if (c->kerr == nullptr) return fail(WD_ERR_STATE, "no device error word");
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(c->kerr, ns);
+  WD_CHECK_LAUNCH();
+  return WD_OK;
+}
+
 // Last hop of K_hat fused with the Chebyshev recurrence step (FP32):
 //   Ks = y + alpha D^dag_eo x  (y = M_hat s, x = D^dag_oe y),
 //   out = ca (v + cmu s - Ks) - cb sprev.

@@ -78,14 +78,17 @@ __device__ __forceinline__ long long gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// wait for the completion of the phase with the given parity; false after TT_WAIT_NS
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+// wait for the completion of the phase with the given parity; false after ns
+__device__ __forceinline__ bool mbar_wait_ns(unsigned long long* b, unsigned parity, long long ns) {
   if (mbar_try(b, parity)) return true;
   const long long t0 = gtimer();
   for (unsigned k = 1;; ++k) {
     if (mbar_try(b, parity)) return true;
-    if ((k & 255u) == 0 && gtimer() - t0 > TT_WAIT_NS) return false;
+    if ((k & 255u) == 0 && gtimer() - t0 > ns) return false;
   }
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  return mbar_wait_ns(b, parity, TT_WAIT_NS);
 }
 // global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte
 // aligned), completion counted on the barrier

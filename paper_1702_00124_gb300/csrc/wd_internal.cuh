@@ -534,6 +534,9 @@ Field wrap_f64(wd_ctx* c, const double* p);
 inline Reduce reducer(wd_ctx* c) { return Reduce{c->red_partial, c->red_counter, c->red_out}; }
 constexpr int RED_MAX_BLOCKS = 1 << 16;
 
+// bounded-wait self-test (dslash_f32.cu)
+int wait_selftest(wd_ctx* c, long long ns);
+
 // operator layer (dslash.cu)
 // in_cg: the launch belongs to a queued CG iteration and returns at once when
 // the solver state carries a stop flag; norm_cg: also form pAp = |out|^2.

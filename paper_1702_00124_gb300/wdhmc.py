@@ -127,6 +127,7 @@ _SIG = {
     "wd_set_residual": ([_P, _I], _I),
     "wd_set_stencil": ([_P, _I], _I),
     "wd_kernel_status": ([_P, C.POINTER(C.c_uint)], _I),
+    "wd_selftest_wait_timeout": ([_P, C.c_longlong], _I),
     "wd_set_autotune": ([_P, _I, C.POINTER(_I)], _I),
     "wd_tune_entry": ([_P, _I, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I)], _I),
     "wd_hop_counts": ([_P, C.POINTER(C.c_longlong)], _I),
@@ -318,6 +319,9 @@ class Lattice:
 
     def wd_set_stencil(self, stencil):
         _check(lib.wd_set_stencil(self.h, stencil))
+
+    def wd_selftest_wait_timeout(self, timeout_ns):
+        _check(lib.wd_selftest_wait_timeout(self.h, int(timeout_ns)))
 
     def wd_kernel_status(self):
         w = C.c_uint(0)

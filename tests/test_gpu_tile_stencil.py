@@ -16,7 +16,9 @@ BF16 3e-2 (6e-2 for K_hat), as for the other FP32 and 16-bit operator tests;
 the two kernels against each other 1e-6 (FP32 arithmetic in the same order per
 site, rounding of FMA contractions may differ); the Chebyshev filter at FP32
 1e-5; mixed-precision CG reaches the true relative residual 1e-10 recomputed by
-the oracle.
+the oracle.  The bounded barrier wait of the tile kernel is shown to expire
+with WD_ERR_TIMEOUT (a barrier nothing arrives at, 50 ms bound) and to leave
+the context usable.
 """
 import numpy as np
 import pytest
@@ -144,3 +146,24 @@ def test_stencil_argument_checked(setup):
     with pytest.raises(wd.WdError) as e:
         lat.wd_set_stencil(2)
     assert e.value.code == 1
+
+
+def test_bounded_wait_expires_and_context_stays_usable(setup):
+    """A barrier wait that nothing completes ends after its bound (50 ms here)
+    with WD_ERR_TIMEOUT in the device error word; the context keeps working."""
+    dims, U, psi, lat, gu, wd = setup
+    assert lat.wd_kernel_status() == 0
+    with pytest.raises(wd.WdError) as e:
+        lat.wd_selftest_wait_timeout(1000)          # below the allowed bound
+    assert e.value.code == 1
+    lat.wd_selftest_wait_timeout(50_000_000)
+    with pytest.raises(wd.WdError) as e:
+        lat.wd_kernel_status()
+    assert e.value.code == 6
+    assert lat.wd_kernel_status() == 0              # read and cleared
+    src = lattice.mask(psi, dims, 1)
+    ref = lattice.mask(wilson.hop(U, src), dims, 0)
+    out = lat.half_spinor()
+    _with(lat, 1, lambda: lat.wd_hop(0, False, wd.F32, gu.pack(lat, psi, 1), out))
+    assert gu.site_rel_err(gu.unpack(lat, out, 0), ref, 0, dims) < 1e-5
+    assert lat.wd_kernel_status() == 0
