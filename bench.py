@@ -363,6 +363,11 @@ def kernel_case(args):
     """K_hat alone on the workload's lattice: the launch sequence ncu captures."""
     import torch
     from paper_1702_00124_gb300 import synthetic, wdhmc as wd
+    if args.kernel_case == "batched":
+        for k in range(args.reps):
+            r = batched_workload_run(wd)
+            print(f"kernel case batched (24 lattices x 4 rhs, call {k}): " + json.dumps(r))
+        return
     w = WORKLOADS[args.workload]
     dims = w["dims"]
     U = synthetic.gauge_field(dims, w["a"], synthetic.SEED_BASE + 4)
@@ -650,7 +655,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-vs-FP64 and e2e measurements")
     ap.add_argument("--kernel-case", choices=["khat_f32_recon12", "khat_bf16_recon12", "khat_f64", "khat_df",
-                                              "poly_f32_recon12"],
+                                              "poly_f32_recon12", "batched"],
                     help="only apply K_hat --reps times on the workload (for ncu captures); prints no JSON")
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--profile", action="store_true", help="kernel case: time every hop with CUDA events")

@@ -72,12 +72,29 @@ __device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& c
   return !a.use_flags || a.st[s].flag == 0;
 }
 
-__device__ __forceinline__ void b_block_partial(const BArgs& a, double (&v)[B_MAXR]) {
-  __shared__ double sh[B_MAXR * 32];
-  block_sum<B_MAXR>(v, sh);
-  if (threadIdx.x == 0) {
+// Per-block partial sums of every right-hand side: v[r] holds the thread's
+// value for its system (zero elsewhere).  FP32 sums (warp shuffles, then the
+// warps in order by lane r of warp 0), stored as FP64; GB300 issues FP64 at
+// 1/64 of the FP32 rate, and eight FP64 shuffle trees per thread cost more
+// than the hop itself.  Deterministic: a fixed order at every level.
+__device__ __forceinline__ void b_block_partial(const BArgs& a, float (&v)[B_MAXR]) {
+  __shared__ float sh[B_MAXR * 32];
 #pragma unroll
-    for (int k = 0; k < B_MAXR; ++k) a.partial[(long)blockIdx.x * B_MAXR + k] = v[k];
+  for (int k = 0; k < B_MAXR; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < B_MAXR; ++k) sh[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0 && lane < B_MAXR) {
+    const int nw = (blockDim.x + 31) >> 5;
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += sh[lane * 32 + w];
+    a.partial[(long)blockIdx.x * B_MAXR + lane] = (double)t;
   }
 }
 
@@ -86,9 +103,9 @@ __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy
   const BLat* L;
   long cb;
   int r, s;
-  double v[B_MAXR];
+  float v[B_MAXR];
 #pragma unroll
-  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.0;
+  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
   if (b_locate(a, L, cb, r, s)) {
     const long stride = L->g.Vh * L->nr;
     SpIL in{L->f[fin], stride, L->nr, r}, out{L->f[fout], stride, L->nr, r};
@@ -118,9 +135,9 @@ __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy
       for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
     }
     if constexpr (NORM) {
-      double q = 0.0;
+      float q = 0.f;
 #pragma unroll
-      for (int j = 0; j < 12; ++j) q += (double)acc[j].r * acc[j].r + (double)acc[j].i * acc[j].i;
+      for (int j = 0; j < 12; ++j) q = fmaf(acc[j].r, acc[j].r, fmaf(acc[j].i, acc[j].i, q));
 #pragma unroll
       for (int k = 0; k < B_MAXR; ++k)
         if (k == r) v[k] = q;
@@ -135,9 +152,9 @@ __global__ void __launch_bounds__(256) k_bupdate(BArgs a) {
   const BLat* L;
   long cb;
   int r, s;
-  double v[B_MAXR];
+  float v[B_MAXR];
 #pragma unroll
-  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.0;
+  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
   if (b_locate(a, L, cb, r, s)) {
     const long stride = L->g.Vh * L->nr;
     const float al = (float)a.st[s].alpha;
@@ -159,7 +176,7 @@ __global__ void __launch_bounds__(256) k_bupdate(BArgs a) {
     R.store(cb, rv);
 #pragma unroll
     for (int k = 0; k < B_MAXR; ++k)
-      if (k == r) v[k] = (double)q;
+      if (k == r) v[k] = q;
   }
   b_block_partial(a, v);
 }
@@ -181,19 +198,27 @@ __global__ void __launch_bounds__(256) k_bpupdate(BArgs a) {
   P.store(cb, pv);
 }
 
-// Per-system totals of the block partials, in block order, then the CG
-// scalar step.  mode 0: pAp -> alpha; mode 1: |r|^2 -> beta, flags.
-__global__ void k_breduce(const BLat* lats, int nlat, CGState* st, const double* partial, int mode) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// Per-system totals of the block partials, then the CG scalar step; one block
+// per system: thread t adds the partials of blocks t, t + blockDim, ... in
+// order, the block adds the threads in a fixed tree (deterministic).
+// mode 0: pAp -> alpha; mode 1: |r|^2 -> beta, flags.
+constexpr int BRED_THREADS = 128;
+__global__ void __launch_bounds__(BRED_THREADS) k_breduce(const BLat* lats, int nlat, CGState* st,
+                                                          const double* partial, int mode) {
+  const int s = blockIdx.x;
   int l = 0;
   while (l < nlat && s >= lats[l].sys0 + lats[l].nr) ++l;
-  if (l >= nlat || s < lats[l].sys0) return;
+  if (l >= nlat || s < lats[l].sys0) return;     // the same for the whole block
   CGState& S = st[s];
-  if (S.flag != 0) return;
+  if (S.flag != 0) return;                        // read before thread 0 may change it
   const BLat& L = lats[l];
   const int r = s - L.sys0;
-  double tot = 0.0;
-  for (int b = 0; b < L.nblocks; ++b) tot += partial[(long)(L.block0 + b) * B_MAXR + r];
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < L.nblocks; b += blockDim.x) v[0] += partial[(long)(L.block0 + b) * B_MAXR + r];
+  __shared__ double sh[32];
+  block_sum<1>(v, sh);
+  if (threadIdx.x != 0) return;
+  const double tot = v[0];
   if (!isfinite(tot)) { S.flag |= FLAG_NAN; return; }
   if (mode == 0) {
     S.pAp = tot;
@@ -334,7 +359,7 @@ static int b_khat(wd_batch* b, int fin, int fout, bool norm) {
   WD_TRY(b_hop(b, 1, false, fin, BF_T1, -1, false));
   WD_TRY(b_hop(b, 0, false, BF_T1, BF_T2, fin, norm));
   if (norm) {
-    k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 0);
+    k_breduce<<<b->S, BRED_THREADS, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 0);
     b->launches += 1;
   }
   WD_TRY(b_hop(b, 1, true, BF_T2, BF_T1, -1, false));
@@ -348,7 +373,7 @@ static int b_iteration(wd_batch* b) {
   int s = b_khat(b, BF_P, BF_AP, true);
   if (s == WD_OK) {
     k_bupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
-    k_breduce<<<nblocks(b->S, 128), 128, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 1);
+    k_breduce<<<b->S, BRED_THREADS, 0, b->stream>>>(b->lat_d, (int)b->lat_h.size(), b->st_d, b->partial, 1);
     k_bpupdate<<<b->nblocks, b->threads, 0, b->stream>>>(b_args(b, 0));
     b->launches += 3;
   }

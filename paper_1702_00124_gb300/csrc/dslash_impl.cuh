@@ -60,6 +60,26 @@ __device__ __forceinline__ void su3_dag_mul(const cpx<T> (&U)[9], const cpx<T> (
       o[3 * a + c] = cmulc(U[c], h[3 * a]) + cmulc(U[3 + c], h[3 * a + 1]) + cmulc(U[6 + c], h[3 * a + 2]);
 }
 
+// |s|^2 of one site for a grid sum, returned in FP64.  FP32 sites are summed
+// in FP32 (24 terms, relative error ~1e-6): GB300 issues FP64 at 1/64 of the
+// FP32 rate, and 24 FP64 FMAs per site cost as much as the stencil's loads.
+template <class T> __device__ __forceinline__ double site_norm2(const cpx<T> (&s)[12]) {
+  if constexpr (std::is_same<T, float>::value) {
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) q = fmaf(s[j].r, s[j].r, fmaf(s[j].i, s[j].i, q));
+    return (double)q;
+  } else {
+    double q = 0.0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const double re = (double)s[j].r, im = (double)s[j].i;
+      q += re * re + im * im;
+    }
+    return q;
+  }
+}
+
 template <class In, class Out, class Y, class G>
 struct HopArgs {
   Geom g;
@@ -135,13 +155,7 @@ __global__ void __launch_bounds__(MAXT) k_hop(HopArgs<In, Out, Y, G> a) {
 #pragma unroll
       for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
     }
-    if constexpr (NORM) {
-#pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const double re = (double)acc[j].r, im = (double)acc[j].i;
-        part[0] += re * re + im * im;
-      }
-    }
+    if constexpr (NORM) part[0] = site_norm2(acc);
     a.out.store(cb, acc);
   }
   if constexpr (NORM) {

@@ -224,13 +224,7 @@ __global__ void __launch_bounds__(HOP_ST_THREADS, hop_minb<In>()) k_hop_st(HopAr
 #pragma unroll
       for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
     }
-    if constexpr (NORM) {
-#pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const double re = (double)acc[j].r, im = (double)acc[j].i;
-        part[0] += re * re + im * im;
-      }
-    }
+    if constexpr (NORM) part[0] = site_norm2(acc);
     a.out.store(cb, acc);
   }
   if constexpr (NORM) {

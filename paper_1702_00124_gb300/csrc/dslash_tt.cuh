@@ -387,13 +387,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         }
         if (bad) break;
       }
-      if constexpr (NORM) {
-#pragma unroll
-        for (int j = 0; j < 12; ++j) {
-          const double re = (double)acc[j].r, im = (double)acc[j].i;
-          part += re * re + im * im;
-        }
-      }
+      if constexpr (NORM) part += site_norm2(acc);
       a.out.store(cb, acc);
     }
     if (bad) {
