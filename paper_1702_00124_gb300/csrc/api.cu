@@ -93,6 +93,8 @@ int wd_context_create(const int dims[4], void* stream, wd_ctx** out) {
   *out = nullptr;
   for (int m = 0; m < 4; ++m)
     if (dims[m] < 2 || dims[m] % 2 != 0) return fail(WD_ERR_ARG, "every lattice extent must be even and >= 2");
+  if ((long long)dims[0] * dims[1] * dims[2] * dims[3] >= (1LL << 31))
+    return fail(WD_ERR_ARG, "the lattice must have fewer than 2^31 sites");
   wd_ctx* c = new (std::nothrow) wd_ctx();
   if (!c) return fail(WD_ERR_ARG, "out of host memory");
   for (int m = 0; m < 4; ++m) c->g.L[m] = dims[m];

@@ -66,8 +66,9 @@ __device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& c
   L = a.lats + a.block_lat[blockIdx.x];
   const long item = (long)(blockIdx.x - L->block0) * blockDim.x + threadIdx.x;
   if (item >= L->g.Vh * L->nr) return false;
-  cb = item / L->nr;
-  r = (int)(item - cb * L->nr);
+  const unsigned it = (unsigned)item, nr = (unsigned)L->nr;   // Vh * nr < 2^31 (checked at creation)
+  cb = (long)(it / nr);
+  r = (int)(it - (unsigned)cb * nr);
   s = L->sys0 + r;
   return !a.use_flags || a.st[s].flag == 0;
 }
@@ -453,6 +454,8 @@ int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const i
   for (int l = 0; l < nlat; ++l) {
     if (!ctxs[l] || !ctxs[l]->have_gauge) return fail(WD_ERR_STATE, "wd_batch_create: every context needs a gauge field");
     if (nrhs[l] < 1 || nrhs[l] > B_MAXR) return fail(WD_ERR_ARG, "wd_batch_create: 1 <= nrhs <= 8 per lattice");
+    if (ctxs[l]->g.Vh * (long)nrhs[l] >= (1L << 31))
+      return fail(WD_ERR_ARG, "wd_batch_create: Vh * nrhs must stay below 2^31 per lattice");
     if (ctxs[l]->stream != ctxs[0]->stream) return fail(WD_ERR_ARG, "wd_batch_create: contexts must share a stream");
   }
   wd_batch* b = new (std::nothrow) wd_batch();

@@ -112,12 +112,16 @@ struct Geom {
   int L[4];
   int Lh;      // Lx / 2
   long V, Vh;
+  // site index -> coordinates in 32-bit arithmetic (contexts have V < 2^31):
+  // a 64-bit division by a runtime divisor is a long emulated sequence, and
+  // every stencil thread needs three of them
   __host__ __device__ __forceinline__ void coords(long cb, int par, int c[4]) const {
-    int xh = (int)(cb % Lh);
-    long r = cb / Lh;
-    c[1] = (int)(r % L[1]); r /= L[1];
-    c[2] = (int)(r % L[2]);
-    c[3] = (int)(r / L[2]);
+    const unsigned u = (unsigned)cb, lh = (unsigned)Lh, l1 = (unsigned)L[1], l2 = (unsigned)L[2];
+    const unsigned r0 = u / lh, r1 = r0 / l1, r2 = r1 / l2;
+    const int xh = (int)(u - r0 * lh);
+    c[1] = (int)(r0 - r1 * l1);
+    c[2] = (int)(r1 - r2 * l2);
+    c[3] = (int)r2;
     c[0] = 2 * xh + ((par + c[1] + c[2] + c[3]) & 1);
   }
   __host__ __device__ __forceinline__ long cb_of(int x, int y, int z, int t) const {
