@@ -350,9 +350,10 @@ def batched_workload_run(wd):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     info = batch.wd_batch_info()
+    shape = batch.wd_batch_shape()
     out = {"s": dt, "systems": info["systems"], "systems_per_s": info["systems"] / dt,
            "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
-           "max_iters": max(i["iters"] for i in infos), "block_threads": info["threads"]}
+           "max_iters": max(i["iters"] for i in infos), "tuned_tile_shape": shape}
     batch.close()
     for lat in lats:
         lat.close()

@@ -438,13 +438,23 @@ int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
  * residual p->tol.  p->check_every iterations (default 16) run between host
  * checks, as one captured CUDA graph when use_graph (systems that have
  * converged return at once inside the graph).  infos: one per system, in
- * lattice order, or NULL.  The first call times the candidate block sizes of
- * the batched kernels on K_hat b and keeps the fastest. */
+ * lattice order, or NULL.  The first call times the candidate tile shapes of
+ * the batched kernels (items per block, right-hand sides per thread of the
+ * hop; wd_batch_shape) on K_hat b and keeps the fastest. */
 int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const wd_cg_params* p, int use_graph,
                 wd_cg_info* infos);
 /* Systems, block size chosen by the tuner, kernels launched so far (no
  * counterpart in the paper). */
 int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches);
+/* Tile shape of the batched kernels chosen by the tuner (no counterpart in the
+ * paper): (site, rhs) items per block, and right-hand sides of one site that
+ * one thread of the batched hop applies its link to (1, 2 or 4; the link is
+ * loaded and rebuilt once for them).  Either pointer may be NULL. */
+int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread);
+/* Fix the tile shape instead of tuning it (no counterpart in the paper):
+ * items_per_block 64, 128 or 256; rhs_per_thread 1, 2 or 4 dividing every
+ * lattice's nrhs.  WD_ERR_ARG otherwise; the batch is unchanged then. */
+int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread);
 
 /* ---- allocation-free K_hat ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -99,51 +99,113 @@ __device__ __forceinline__ void b_block_partial(const BArgs& a, float (&v)[B_MAX
   }
 }
 
-template <bool DAG, bool XPAY, bool NORM, bool R12>
+// One direction of the hop for RPT right-hand sides of one site: the link is
+// loaded and rebuilt once and applied to the RPT neighbour spinors (consecutive
+// in the interleaved layout).
+template <int MU, bool DAG, int RPT, class G>
+__device__ __forceinline__ void bhop_dir(const Geom& g, int par, long cb, const int (&c)[4], const float4* in,
+                                         long stride, int nr, int r0, const G& gauge, cpx<float> (&acc)[RPT][12]) {
+  constexpr int SF = DAG ? +1 : -1;
+#pragma unroll
+  for (int fb = 0; fb < 2; ++fb) {
+    const bool fwd = fb == 0;
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    if (fwd) n[MU] = (n[MU] + 1 == g.L[MU]) ? 0 : n[MU] + 1;
+    else n[MU] = (n[MU] == 0) ? g.L[MU] - 1 : n[MU] - 1;
+    const long nb = g.cb_of(n[0], n[1], n[2], n[3]);
+    cpx<float> U[9];
+    if (fwd) gauge.load(MU, par, cb, U);
+    else gauge.load(MU, 1 - par, nb, U);
+    const bool flip = MU == 3 && (fwd ? c[3] == g.L[3] - 1 : c[3] == 0);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      cpx<float> sp[12], h[6], u[6];
+      SpF32{const_cast<float4*>(in), stride}.loadT(nb * nr + r0 + k, sp);
+      if (fwd) spin_project<MU, SF>(sp, h);
+      else spin_project<MU, -SF>(sp, h);
+      if (flip) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) h[j] = mk<float>(-h[j].r, -h[j].i);
+      }
+      if (fwd) {
+        su3_mul(U, h, u);
+        spin_accum<MU, SF>(acc[k], u);
+      } else {
+        su3_dag_mul(U, h, u);
+        spin_accum<MU, -SF>(acc[k], u);
+      }
+    }
+  }
+}
+
+// Batched hop; every thread handles RPT consecutive (site, rhs) items of its
+// lattice (nr % RPT == 0, so they share one site), blocks of blockDim.x * RPT
+// items as laid out by b_layout.  Systems with a stop flag are not written.
+template <bool DAG, bool XPAY, bool NORM, bool R12, int RPT>
 __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy) {
-  const BLat* L;
-  long cb;
-  int r, s;
+  const BLat* L = a.lats + a.block_lat[blockIdx.x];
+  const long item0 = (long)(blockIdx.x - L->block0) * (blockDim.x * RPT) + (long)threadIdx.x * RPT;
   float v[B_MAXR];
 #pragma unroll
   for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
-  if (b_locate(a, L, cb, r, s)) {
+  bool act[RPT];
+  bool any = false;
+  long cb = 0;
+  int r0 = 0;
+  if (item0 < L->g.Vh * L->nr) {
+    const unsigned it = (unsigned)item0, nr = (unsigned)L->nr;   // Vh * nr < 2^31 (checked at creation)
+    cb = (long)(it / nr);
+    r0 = (int)(it - (unsigned)cb * nr);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      act[k] = !a.use_flags || a.st[L->sys0 + r0 + k].flag == 0;
+      any = any || act[k];
+    }
+  }
+  if (any) {
     const long stride = L->g.Vh * L->nr;
-    SpIL in{L->f[fin], stride, L->nr, r}, out{L->f[fout], stride, L->nr, r};
     int c[4];
     L->g.coords(cb, a.out_par, c);
-    cpx<float> acc[12];
+    cpx<float> acc[RPT][12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) acc[j] = mk<float>(0, 0);
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[k][j] = mk<float>(0, 0);
+    const float4* in = L->f[fin];
     if constexpr (R12) {
       GF32R12 G{L->g12, L->g.Vh};
-      hop_dir<0, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<1, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<2, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<3, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      bhop_dir<0, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<1, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<2, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<3, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
     } else {
       GF32 G{L->g18, L->g.Vh};
-      hop_dir<0, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<1, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<2, DAG>(L->g, a.out_par, cb, c, in, G, acc);
-      hop_dir<3, DAG>(L->g, a.out_par, cb, c, in, G, acc);
+      bhop_dir<0, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<1, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<2, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<3, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
     }
-    if constexpr (XPAY) {
-      cpx<float> yv[12];
-      SpIL{L->f[fy], stride, L->nr, r}.loadT(cb, yv);
-      const float al = (float)(-L->kappa * L->kappa);
 #pragma unroll
-      for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
+    for (int k = 0; k < RPT; ++k) {
+      if (!act[k]) continue;
+      const int r = r0 + k;
+      if constexpr (XPAY) {
+        cpx<float> yv[12];
+        SpIL{L->f[fy], stride, L->nr, r}.loadT(cb, yv);
+        const float al = (float)(-L->kappa * L->kappa);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) acc[k][j] = yv[j] + al * acc[k][j];
+      }
+      if constexpr (NORM) {
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) q = fmaf(acc[k][j].r, acc[k][j].r, fmaf(acc[k][j].i, acc[k][j].i, q));
+#pragma unroll
+        for (int m = 0; m < B_MAXR; ++m)
+          if (m == r) v[m] = q;
+      }
+      SpIL{L->f[fout], stride, L->nr, r}.store(cb, acc[k]);
     }
-    if constexpr (NORM) {
-      float q = 0.f;
-#pragma unroll
-      for (int j = 0; j < 12; ++j) q = fmaf(acc[j].r, acc[j].r, fmaf(acc[j].i, acc[j].i, q));
-#pragma unroll
-      for (int k = 0; k < B_MAXR; ++k)
-        if (k == r) v[k] = q;
-    }
-    out.store(cb, acc);
   }
   if constexpr (NORM) b_block_partial(a, v);
 }
@@ -276,7 +338,8 @@ struct wd_batch {
   std::vector<BLat> lat_h;
   BLat* lat_d = nullptr;
   int S = 0;                     // systems
-  int threads = 128;             // block size (autotuned on first use)
+  int threads = 128;             // items (site, rhs) per block (autotuned on first use)
+  int rpt = 1;                   // right-hand sides per thread of the batched hop (autotuned)
   bool tuned = false;
   std::vector<int> block_lat_h;
   int* block_lat_d = nullptr;
@@ -329,7 +392,12 @@ static BArgs b_args(wd_batch* b, int out_par) {
 static int b_hop(wd_batch* b, int out_par, bool dag, int fin, int fout, int fy, bool norm) {
   const BArgs a = b_args(b, out_par);
   const bool r12 = b->lat_h[0].recon == 12;
-#define WD_BH(D, X, N, R) k_bhop<D, X, N, R><<<b->nblocks, b->threads, 0, b->stream>>>(a, fin, fout, fy)
+#define WD_BH(D, X, N, R)                                                                                 \
+  do {                                                                                                    \
+    if (b->rpt == 4) k_bhop<D, X, N, R, 4><<<b->nblocks, b->threads / 4, 0, b->stream>>>(a, fin, fout, fy); \
+    else if (b->rpt == 2) k_bhop<D, X, N, R, 2><<<b->nblocks, b->threads / 2, 0, b->stream>>>(a, fin, fout, fy); \
+    else k_bhop<D, X, N, R, 1><<<b->nblocks, b->threads, 0, b->stream>>>(a, fin, fout, fy);                \
+  } while (0)
   if (r12) {
     if (!dag) {
       if (fy < 0) WD_BH(false, false, false, true);
@@ -405,13 +473,25 @@ static int b_leave(wd_batch* b) {
   return WD_OK;
 }
 
-// Time the batched K_hat for each candidate block size; keep the fastest.
+// Tile-shape tuner: time the batched K_hat for each candidate shape (items
+// per block, right-hand sides per thread of the hop) and keep the fastest.
 // Rounds with the candidate order rotated; median per candidate; the default
-// 128 is replaced only by a candidate at least 3 % faster.
+// (128 items, one rhs per thread) is replaced only by a candidate at least 3 %
+// faster.  A shape with rpt > 1 needs nr % rpt == 0 on every lattice.
+struct BShape {
+  int threads, rpt;
+};
 static int b_autotune(wd_batch* b) {
-  constexpr int NC = 3, ROUNDS = 5;
-  const int cand[NC] = {128, 256, 64};
-  std::vector<float> t[NC];
+  constexpr int ROUNDS = 5;
+  const BShape all[] = {{128, 1}, {256, 1}, {64, 1}, {128, 2}, {256, 2}, {128, 4}, {256, 4}};
+  std::vector<BShape> cand;
+  for (const BShape& c : all) {
+    bool ok = true;
+    for (const BLat& L : b->lat_h) ok = ok && (L.nr % c.rpt == 0);
+    if (ok) cand.push_back(c);
+  }
+  const int NC = (int)cand.size();
+  std::vector<std::vector<float>> t(NC);
   cudaEvent_t e0, e1;
   WD_CUDA(cudaEventCreate(&e0));
   WD_CUDA(cudaEventCreate(&e1));
@@ -419,7 +499,8 @@ static int b_autotune(wd_batch* b) {
   for (int r = 0; r < ROUNDS; ++r) {
     for (int j = 0; j < NC; ++j) {
       const int k = (j + r) % NC;
-      WD_TRY(b_layout(b, cand[k]));
+      WD_TRY(b_layout(b, cand[k].threads));
+      b->rpt = cand[k].rpt;
       cudaEventRecord(e0, b->stream);
       WD_TRY(b_khat(b, BF_P, BF_AP, false));
       cudaEventRecord(e1, b->stream);
@@ -431,7 +512,7 @@ static int b_autotune(wd_batch* b) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  float med[NC];
+  std::vector<float> med(NC);
   for (int k = 0; k < NC; ++k) {
     std::sort(t[k].begin(), t[k].end());
     med[k] = t[k][t[k].size() / 2];
@@ -439,7 +520,8 @@ static int b_autotune(wd_batch* b) {
   int pick = 0;
   for (int k = 1; k < NC; ++k)
     if (med[k] < 0.97f * med[pick]) pick = k;
-  WD_TRY(b_layout(b, cand[pick]));
+  WD_TRY(b_layout(b, cand[pick].threads));
+  b->rpt = cand[pick].rpt;
   b->tuned = true;
   return WD_OK;
 }
@@ -674,6 +756,28 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
   }
   WD_TRY(b_leave(b));
   return status;
+}
+
+int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread) {
+  if (!b) return fail(WD_ERR_ARG, "null batch");
+  if (items_per_block != 64 && items_per_block != 128 && items_per_block != 256)
+    return fail(WD_ERR_ARG, "wd_batch_set_shape: items_per_block must be 64, 128 or 256");
+  if (rhs_per_thread != 1 && rhs_per_thread != 2 && rhs_per_thread != 4)
+    return fail(WD_ERR_ARG, "wd_batch_set_shape: rhs_per_thread must be 1, 2 or 4");
+  for (const BLat& L : b->lat_h)
+    if (L.nr % rhs_per_thread != 0)
+      return fail(WD_ERR_ARG, "wd_batch_set_shape: rhs_per_thread must divide every lattice's nrhs");
+  WD_TRY(b_layout(b, items_per_block));
+  b->rpt = rhs_per_thread;
+  b->tuned = true;
+  return WD_OK;
+}
+
+int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread) {
+  if (!b) return fail(WD_ERR_ARG, "null batch");
+  if (items_per_block) *items_per_block = b->threads;
+  if (rhs_per_thread) *rhs_per_thread = b->rpt;
+  return WD_OK;
 }
 
 int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches) {

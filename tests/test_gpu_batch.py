@@ -4,7 +4,10 @@ Small batch (three uneven lattices, 1-3 right-hand sides, different kappa):
 batched K_hat (FP32, interleaved right-hand sides, one launch for all
 lattices) per system vs the oracle (2e-5 per site); batched mixed-precision
 CG, with and without CUDA-graph replay, reaches the FP64 true residual 1e-10
-recomputed by the oracle and matches the single-system solve (1e-8).
+recomputed by the oracle and matches the single-system solve (1e-8).  A second
+small batch with four right-hand sides per lattice runs the batched K_hat in
+every tile shape (64-256 items per block, one, two or four right-hand sides per
+thread of the hop; 2e-5 per site) and CG with two and four per thread (1e-10).
 
 The batched workload at full size (24 lattices: 8 x 8^4, 8 x 12^3 x 24,
 8 x 16^3 x 32, links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian
@@ -85,6 +88,68 @@ def test_batched_cg(small, use_graph):
             lat.cg_solve(k, gu.pack(lat, rhs[r], 0), xs1, wd.cg_params(tol=1e-10, prec=wd.F32))
             assert gu.rel_norm_err(xr, gu.unpack(lat, xs1, 0)) < 1e-8
             s += 1
+
+
+@pytest.fixture(scope="module")
+def small4():
+    """Three uneven lattices with four right-hand sides each: every tile shape
+    (one, two or four right-hand sides per thread of the batched hop) applies."""
+    import torch
+    from paper_1702_00124_gb300 import wdhmc as wd
+    from tests import gpu_util as gu
+    spec = [((4, 4, 4, 4), 0.5, 0.12, 4), ((6, 4, 6, 10), 0.4, 0.128, 4), ((8, 8, 8, 8), 0.4, 0.125, 4)]
+    stream = torch.cuda.current_stream()
+    items = [_make(d, a, k, nr, 1900 + 10 * i, wd, gu, stream) for i, (d, a, k, nr) in enumerate(spec)]
+    lats = [it[1] for it in items]
+    batch = wd.Batch(lats, [s[2] for s in spec], [s[3] for s in spec])
+    yield spec, items, batch, wd, gu
+    batch.close()
+    for lat in lats:
+        lat.close()
+
+
+SHAPES = [(128, 1), (64, 1), (256, 1), (128, 2), (256, 2), (128, 4), (256, 4)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{t}x{r}" for t, r in SHAPES])
+def test_batched_khat_every_tile_shape(small4, shape):
+    spec, items, batch, wd, gu = small4
+    batch.wd_batch_set_shape(*shape)
+    assert batch.wd_batch_shape() == dict(items_per_block=shape[0], rhs_per_thread=shape[1])
+    ins = [_pack_rhs(it[1], gu, it[2]) for it in items]
+    outs = [torch_zeros_like(x) for x in ins]
+    batch.wd_batch_mdagm(ins, outs)
+    for (dims, a, k, nr), (U, lat, rhs), o in zip(spec, items, outs):
+        for r in range(nr):
+            got = gu.unpack(lat, o[r * 24 * lat.Vh:(r + 1) * 24 * lat.Vh].contiguous(), 0)
+            assert gu.site_rel_err(got, wilson.apply_Khat(U, rhs[r], k), 0, dims) < 2e-5
+
+
+@pytest.mark.parametrize("shape", [(128, 2), (128, 4)], ids=["128x2", "128x4"])
+def test_batched_cg_multi_rhs_per_thread(small4, shape):
+    """CG with the stop flags per system: right-hand sides of one thread converge
+    at different iterations, so each thread writes only its running systems."""
+    spec, items, batch, wd, gu = small4
+    batch.wd_batch_set_shape(*shape)
+    bs = [_pack_rhs(it[1], gu, it[2]) for it in items]
+    xs = [torch_zeros_like(b) for b in bs]
+    infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), True)
+    s = 0
+    for (dims, a, k, nr), (U, lat, rhs), x in zip(spec, items, xs):
+        for r in range(nr):
+            xr = gu.unpack(lat, x[r * 24 * lat.Vh:(r + 1) * 24 * lat.Vh].contiguous(), 0)
+            res = np.linalg.norm(rhs[r] - wilson.apply_Khat(U, xr, k)) / np.linalg.norm(rhs[r])
+            assert res <= 1.01e-10, (dims, r, res, infos[s])
+            s += 1
+    assert len({i["iters"] for i in infos}) > 1       # systems did stop at different iterations
+
+
+def test_batched_shape_arguments_checked(small):
+    spec, items, batch, wd, gu = small
+    for bad in ((96, 1), (128, 3), (128, 2)):          # nrhs 3 and 1 are not multiples of 2
+        with pytest.raises(wd.WdError) as e:
+            batch.wd_batch_set_shape(*bad)
+        assert e.value.code == 1
 
 
 @pytest.mark.slow
