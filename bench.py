@@ -324,7 +324,8 @@ def replica_throughput(world, steps, t_max):
 def batched_workload_run(wd):
     """The batched workload: 24 lattices (8 x 8^4, 8 x 12^3 x 24, 8 x 16^3 x 32),
     links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian right-hand sides
-    each, mixed-precision CG of all 96 systems to 1e-10 (CUDA-graph chunks)."""
+    each, mixed-precision CG of all 96 systems to 1e-10 (CUDA-graph chunks,
+    reliable updates with K_hat x in double-float as in the trajectory)."""
     import torch
     from paper_1702_00124_gb300 import synthetic
     work = synthetic.batched_workload()
@@ -335,6 +336,7 @@ def batched_workload_run(wd):
         lat = wd.Lattice(w["dims"], stream=stream)
         lat.wd_gauge_load(torch.from_numpy(U.view(np.float64).reshape(-1)).cuda())
         lat.wd_set_recon(wd.RECON_12)
+        lat.wd_set_residual(RESIDUAL_MODE)
         b = torch.empty(w["nrhs"] * 24 * lat.Vh, dtype=torch.float64, device="cuda")
         for r in range(w["nrhs"]):
             lat.gaussian_draw(0, 0, w["seed"], 10 + r, b[r * 24 * lat.Vh:(r + 1) * 24 * lat.Vh])

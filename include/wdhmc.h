@@ -435,7 +435,8 @@ int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
 /* CG (Section 2: the iterative solver of K) for every system from x = 0,
  * mixed precision: FP32 batched iterations,
  * FP64 reliable updates per system (through its context) to the FP64 true
- * residual p->tol.  p->check_every iterations (default 16) run between host
+ * residual p->tol; K_hat x of a reliable update is formed in double-float
+ * when the system's context has wd_set_residual(ctx, 1).  p->check_every iterations (default 16) run between host
  * checks, as one captured CUDA graph when use_graph (systems that have
  * converged return at once inside the graph).  infos: one per system, in
  * lattice order, or NULL.  The first call times the candidate tile shapes of

@@ -720,7 +720,21 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
           WD_CUDA(cudaStreamWaitEvent(c->stream, b->ev_out, 0));
         }
         WD_TRY(axpby(c, 1.0, xf, 1.0, t, xf));
-        WD_TRY(apply_khat(c, L.kappa, xf, t, t1, t2, false, false));
+        if (c->resid_dd && c->gauge_dd) {
+          // K_hat x in double-float when the lattice's context selects it (as
+          // the single-system solver's true residual): FP64-class accuracy on
+          // the FP32 pipes, b, x, r and the norm stay FP64
+          Field xd, td, d1, d2;
+          WD_TRY(w.get(WD_DD, &xd));
+          WD_TRY(w.get(WD_DD, &td));
+          WD_TRY(w.get(WD_DD, &d1));
+          WD_TRY(w.get(WD_DD, &d2));
+          WD_TRY(convert(c, xf, xd));
+          WD_TRY(apply_khat(c, L.kappa, xd, td, d1, d2, false, false));
+          WD_TRY(convert(c, td, t));
+        } else {
+          WD_TRY(apply_khat(c, L.kappa, xf, t, t1, t2, false, false));
+        }
         WD_TRY(axpby(c, 1.0, bf, -1.0, t, rr));
         double rr2;
         WD_TRY(norm2(c, rr, &rr2));

@@ -3,8 +3,9 @@
 Small batch (three uneven lattices, 1-3 right-hand sides, different kappa):
 batched K_hat (FP32, interleaved right-hand sides, one launch for all
 lattices) per system vs the oracle (2e-5 per site); batched mixed-precision
-CG, with and without CUDA-graph replay, reaches the FP64 true residual 1e-10
-recomputed by the oracle and matches the single-system solve (1e-8).  A second
+CG, with and without CUDA-graph replay and with the reliable updates' K_hat x
+in FP64 or double-float, reaches the FP64 true residual 1e-10 recomputed by
+the oracle and matches the single-system solve (1e-8).  A second
 small batch with four right-hand sides per lattice runs the batched K_hat in
 every tile shape (64-256 items per block, one, two or four right-hand sides per
 thread of the hop; 2e-5 per site) and CG with two and four per thread (1e-10).
@@ -70,12 +71,19 @@ def torch_zeros_like(x):
     return torch.zeros_like(x)
 
 
-@pytest.mark.parametrize("use_graph", [True, False], ids=["graph", "eager"])
-def test_batched_cg(small, use_graph):
+@pytest.mark.parametrize("use_graph,resid", [(True, 0), (False, 0), (True, 1)],
+                         ids=["graph", "eager", "graph-dfresid"])
+def test_batched_cg(small, use_graph, resid):
     spec, items, batch, wd, gu = small
     bs = [_pack_rhs(it[1], gu, it[2]) for it in items]
     xs = [torch_zeros_like(b) for b in bs]
-    infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), use_graph)
+    for it in items:
+        it[1].wd_set_residual(resid)
+    try:
+        infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), use_graph)
+    finally:
+        for it in items:
+            it[1].wd_set_residual(0)
     s = 0
     for (dims, a, k, nr), (U, lat, rhs), x in zip(spec, items, xs):
         for r in range(nr):
