@@ -345,17 +345,23 @@ def batched_workload_run(wd):
         xs.append(torch.zeros_like(b))
     batch = wd.Batch(lats, [w["kappa"] for w in work], [w["nrhs"] for w in work])
     p = wd.cg_params(tol=1e-10, prec=wd.F32)
-    batch.wd_batch_cg(bs, xs, p, True)          # tunes, captures the graph
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    infos = batch.wd_batch_cg(bs, xs, p, True)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    out = {}
+    # 1: each chunk of 16 iterations as a captured graph of 8 launches per
+    # iteration; 2: one persistent cooperative launch per chunk
+    for mode, name in ((1, "graph"), (2, "persistent")):
+        batch.wd_batch_cg(bs, xs, p, mode)          # tunes (first call), captures the graph
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        infos = batch.wd_batch_cg(bs, xs, p, mode)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[name] = {"s": dt, "systems_per_s": len(infos) / dt,
+                     "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
+                     "max_iters": max(i["iters"] for i in infos)}
     info = batch.wd_batch_info()
-    shape = batch.wd_batch_shape()
-    out = {"s": dt, "systems": info["systems"], "systems_per_s": info["systems"] / dt,
-           "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
-           "max_iters": max(i["iters"] for i in infos), "tuned_tile_shape": shape}
+    best = min(out, key=lambda k: out[k]["s"])
+    out.update({"s": out[best]["s"], "systems": info["systems"], "systems_per_s": out[best]["systems_per_s"],
+                "mode": best, "tuned_tile_shape": batch.wd_batch_shape()})
     batch.close()
     for lat in lats:
         lat.close()

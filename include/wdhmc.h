@@ -436,9 +436,13 @@ int wd_batch_mdagm(wd_batch* b, const double* const* in, double* const* out);
  * mixed precision: FP32 batched iterations,
  * FP64 reliable updates per system (through its context) to the FP64 true
  * residual p->tol; K_hat x of a reliable update is formed in double-float
- * when the system's context has wd_set_residual(ctx, 1).  p->check_every iterations (default 16) run between host
- * checks, as one captured CUDA graph when use_graph (systems that have
- * converged return at once inside the graph).  infos: one per system, in
+ * when the system's context has wd_set_residual(ctx, 1).  p->check_every
+ * iterations (default 16) run between host checks: use_graph = 0 as plain
+ * launches (eight per iteration), 1 as one captured CUDA graph of those
+ * launches, 2 as one persistent cooperative kernel per chunk whose phases are
+ * separated by grid barriers (every block resident; each barrier wait bounded
+ * to two seconds, an expiry returns WD_ERR_TIMEOUT).  Systems that have
+ * converged or wait for a reliable update do no work inside a chunk.  infos: one per system, in
  * lattice order, or NULL.  The first call times the candidate tile shapes of
  * the batched kernels (items per block, right-hand sides per thread of the
  * hop; wd_batch_shape) on K_hat b and keeps the fastest. */

@@ -62,15 +62,51 @@ struct BArgs {
   int use_flags;           // inside CG: systems with a stop flag do no work
 };
 
-__device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& cb, int& r, int& s) {
-  L = a.lats + a.block_lat[blockIdx.x];
-  const long item = (long)(blockIdx.x - L->block0) * blockDim.x + threadIdx.x;
-  if (item >= L->g.Vh * L->nr) return false;
-  const unsigned it = (unsigned)item, nr = (unsigned)L->nr;   // Vh * nr < 2^31 (checked at creation)
-  cb = (long)(it / nr);
-  r = (int)(it - (unsigned)cb * nr);
-  s = L->sys0 + r;
-  return !a.use_flags || a.st[s].flag == 0;
+// The RPT consecutive (site, rhs) items of this thread in block vb of the
+// layout (blocks of blockDim.x * RPT items, lattice after lattice); with
+// nr % RPT == 0 they belong to one site.
+struct BItem {
+  const BLat* L;
+  long cb;
+  int r0;
+  bool valid;
+};
+__device__ __forceinline__ BItem b_item(const BArgs& a, int vb, int rpt) {
+  BItem it;
+  it.L = a.lats + a.block_lat[vb];
+  const long item0 = (long)(vb - it.L->block0) * (blockDim.x * rpt) + (long)threadIdx.x * rpt;
+  it.valid = item0 < it.L->g.Vh * it.L->nr;
+  it.cb = 0;
+  it.r0 = 0;
+  if (it.valid) {
+    const unsigned u = (unsigned)item0, nr = (unsigned)it.L->nr;   // Vh * nr < 2^31 (checked at creation)
+    it.cb = (long)(u / nr);
+    it.r0 = (int)(u - (unsigned)it.cb * nr);
+  }
+  return it;
+}
+// Loads of data the same kernel may have written (COH): the persistent kernel
+// reads fields, sums and solver state that other blocks wrote in an earlier
+// phase, which the read-only path (ld.global.nc) does not allow; ld.global.cg
+// reads them from L2, after the grid barrier's fences.  Separate launches use
+// the read-only path.
+template <bool COH> __device__ __forceinline__ float4 bld(const float4* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH> __device__ __forceinline__ void bload(const float4* f, long stride, long e, cpx<float> (&s)[12]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float4 v = bld<COH>(f + j * stride + e);
+    s[2 * j] = {v.x, v.y};
+    s[2 * j + 1] = {v.z, v.w};
+  }
+}
+// inside CG, systems that carry a stop flag do no work
+template <bool COH> __device__ __forceinline__ bool b_active(const BArgs& a, const BLat* L, int r) {
+  if (!a.use_flags) return true;
+  if constexpr (COH) return __ldcg(&a.st[L->sys0 + r].flag) == 0;
+  else return a.st[L->sys0 + r].flag == 0;
 }
 
 // Per-block partial sums of every right-hand side: v[r] holds the thread's
@@ -78,7 +114,7 @@ __device__ __forceinline__ bool b_locate(const BArgs& a, const BLat*& L, long& c
 // warps in order by lane r of warp 0), stored as FP64; GB300 issues FP64 at
 // 1/64 of the FP32 rate, and eight FP64 shuffle trees per thread cost more
 // than the hop itself.  Deterministic: a fixed order at every level.
-__device__ __forceinline__ void b_block_partial(const BArgs& a, float (&v)[B_MAXR]) {
+__device__ __forceinline__ void b_block_partial(const BArgs& a, int vb, float (&v)[B_MAXR]) {
   __shared__ float sh[B_MAXR * 32];
 #pragma unroll
   for (int k = 0; k < B_MAXR; ++k) {
@@ -95,14 +131,14 @@ __device__ __forceinline__ void b_block_partial(const BArgs& a, float (&v)[B_MAX
     const int nw = (blockDim.x + 31) >> 5;
     float t = 0.f;
     for (int w = 0; w < nw; ++w) t += sh[lane * 32 + w];
-    a.partial[(long)blockIdx.x * B_MAXR + lane] = (double)t;
+    a.partial[(long)vb * B_MAXR + lane] = (double)t;
   }
 }
 
 // One direction of the hop for RPT right-hand sides of one site: the link is
 // loaded and rebuilt once and applied to the RPT neighbour spinors (consecutive
 // in the interleaved layout).
-template <int MU, bool DAG, int RPT, class G>
+template <int MU, bool DAG, int RPT, bool COH, class G>
 __device__ __forceinline__ void bhop_dir(const Geom& g, int par, long cb, const int (&c)[4], const float4* in,
                                          long stride, int nr, int r0, const G& gauge, cpx<float> (&acc)[RPT][12]) {
   constexpr int SF = DAG ? +1 : -1;
@@ -120,7 +156,7 @@ __device__ __forceinline__ void bhop_dir(const Geom& g, int par, long cb, const 
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       cpx<float> sp[12], h[6], u[6];
-      SpF32{const_cast<float4*>(in), stride}.loadT(nb * nr + r0 + k, sp);
+      bload<COH>(in, stride, nb * nr + r0 + k, sp);
       if (fwd) spin_project<MU, SF>(sp, h);
       else spin_project<MU, -SF>(sp, h);
       if (flip) {
@@ -139,30 +175,25 @@ __device__ __forceinline__ void bhop_dir(const Geom& g, int par, long cb, const 
 }
 
 // Batched hop; every thread handles RPT consecutive (site, rhs) items of its
-// lattice (nr % RPT == 0, so they share one site), blocks of blockDim.x * RPT
-// items as laid out by b_layout.  Systems with a stop flag are not written.
-template <bool DAG, bool XPAY, bool NORM, bool R12, int RPT>
-__global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy) {
-  const BLat* L = a.lats + a.block_lat[blockIdx.x];
-  const long item0 = (long)(blockIdx.x - L->block0) * (blockDim.x * RPT) + (long)threadIdx.x * RPT;
+// lattice (nr % RPT == 0, so they share one site) in block vb of the layout.
+// Systems with a stop flag are not written.
+template <bool DAG, bool XPAY, bool NORM, bool R12, int RPT, bool COH = false>
+__device__ __forceinline__ void bhop_body(const BArgs& a, int vb, int fin, int fout, int fy) {
+  const BItem it = b_item(a, vb, RPT);
+  const BLat* L = it.L;
   float v[B_MAXR];
 #pragma unroll
   for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
   bool act[RPT];
   bool any = false;
-  long cb = 0;
-  int r0 = 0;
-  if (item0 < L->g.Vh * L->nr) {
-    const unsigned it = (unsigned)item0, nr = (unsigned)L->nr;   // Vh * nr < 2^31 (checked at creation)
-    cb = (long)(it / nr);
-    r0 = (int)(it - (unsigned)cb * nr);
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      act[k] = !a.use_flags || a.st[L->sys0 + r0 + k].flag == 0;
-      any = any || act[k];
-    }
+  for (int k = 0; k < RPT; ++k) {
+    act[k] = it.valid && b_active<COH>(a, L, it.r0 + k);
+    any = any || act[k];
   }
   if (any) {
+    const long cb = it.cb;
+    const int r0 = it.r0;
     const long stride = L->g.Vh * L->nr;
     int c[4];
     L->g.coords(cb, a.out_par, c);
@@ -174,16 +205,16 @@ __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy
     const float4* in = L->f[fin];
     if constexpr (R12) {
       GF32R12 G{L->g12, L->g.Vh};
-      bhop_dir<0, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<1, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<2, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<3, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<0, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<1, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<2, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<3, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
     } else {
       GF32 G{L->g18, L->g.Vh};
-      bhop_dir<0, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<1, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<2, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
-      bhop_dir<3, DAG, RPT>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<0, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<1, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<2, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
+      bhop_dir<3, DAG, RPT, COH>(L->g, a.out_par, cb, c, in, stride, L->nr, r0, G, acc);
     }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -191,7 +222,7 @@ __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy
       const int r = r0 + k;
       if constexpr (XPAY) {
         cpx<float> yv[12];
-        SpIL{L->f[fy], stride, L->nr, r}.loadT(cb, yv);
+        bload<COH>(L->f[fy], stride, cb * L->nr + r, yv);
         const float al = (float)(-L->kappa * L->kappa);
 #pragma unroll
         for (int j = 0; j < 12; ++j) acc[k][j] = yv[j] + al * acc[k][j];
@@ -207,27 +238,35 @@ __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy
       SpIL{L->f[fout], stride, L->nr, r}.store(cb, acc[k]);
     }
   }
-  if constexpr (NORM) b_block_partial(a, v);
+  if constexpr (NORM) b_block_partial(a, vb, v);
 }
 
-// x += alpha p; r -= alpha Ap; partial |r|^2
-__global__ void __launch_bounds__(256) k_bupdate(BArgs a) {
-  const BLat* L;
-  long cb;
-  int r, s;
+template <bool DAG, bool XPAY, bool NORM, bool R12, int RPT>
+__global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy) {
+  bhop_body<DAG, XPAY, NORM, R12, RPT>(a, blockIdx.x, fin, fout, fy);
+}
+
+// x += alpha p; r -= alpha Ap; partial |r|^2 (RPT items per thread)
+template <int RPT, bool COH = false>
+__device__ __forceinline__ void bupdate_body(const BArgs& a, int vb) {
+  const BItem it = b_item(a, vb, RPT);
   float v[B_MAXR];
 #pragma unroll
   for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
-  if (b_locate(a, L, cb, r, s)) {
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = it.r0 + k;
+    if (!it.valid || !b_active<COH>(a, it.L, r)) continue;
+    const BLat* L = it.L;
     const long stride = L->g.Vh * L->nr;
-    const float al = (float)a.st[s].alpha;
-    SpIL X{L->f[BF_X], stride, L->nr, r}, P{L->f[BF_P], stride, L->nr, r};
-    SpIL R{L->f[BF_R], stride, L->nr, r}, AP{L->f[BF_AP], stride, L->nr, r};
+    const long e = it.cb * L->nr + r;
+    const float al = (float)(COH ? __ldcg(&a.st[L->sys0 + r].alpha) : a.st[L->sys0 + r].alpha);
+    SpIL X{L->f[BF_X], stride, L->nr, r}, R{L->f[BF_R], stride, L->nr, r};
     cpx<float> xv[12], pv[12], rv[12], av[12];
-    X.loadT(cb, xv);
-    P.loadT(cb, pv);
-    R.loadT(cb, rv);
-    AP.loadT(cb, av);
+    bload<COH>(L->f[BF_X], stride, e, xv);
+    bload<COH>(L->f[BF_P], stride, e, pv);
+    bload<COH>(L->f[BF_R], stride, e, rv);
+    bload<COH>(L->f[BF_AP], stride, e, av);
     float q = 0.f;
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
@@ -235,49 +274,55 @@ __global__ void __launch_bounds__(256) k_bupdate(BArgs a) {
       rv[j] = rv[j] - al * av[j];
       q += norm2(rv[j]);
     }
-    X.store(cb, xv);
-    R.store(cb, rv);
+    X.store(it.cb, xv);
+    R.store(it.cb, rv);
 #pragma unroll
-    for (int k = 0; k < B_MAXR; ++k)
-      if (k == r) v[k] = q;
+    for (int m = 0; m < B_MAXR; ++m)
+      if (m == r) v[m] = q;
   }
-  b_block_partial(a, v);
+  b_block_partial(a, vb, v);
 }
+__global__ void __launch_bounds__(256) k_bupdate(BArgs a) { bupdate_body<1>(a, blockIdx.x); }
 
-// p = r + beta p
-__global__ void __launch_bounds__(256) k_bpupdate(BArgs a) {
-  const BLat* L;
-  long cb;
-  int r, s;
-  if (!b_locate(a, L, cb, r, s)) return;
-  const long stride = L->g.Vh * L->nr;
-  const float be = (float)a.st[s].beta;
-  SpIL P{L->f[BF_P], stride, L->nr, r}, R{L->f[BF_R], stride, L->nr, r};
-  cpx<float> pv[12], rv[12];
-  P.loadT(cb, pv);
-  R.loadT(cb, rv);
+// p = r + beta p (RPT items per thread)
+template <int RPT, bool COH = false>
+__device__ __forceinline__ void bpupdate_body(const BArgs& a, int vb) {
+  const BItem it = b_item(a, vb, RPT);
 #pragma unroll
-  for (int j = 0; j < 12; ++j) pv[j] = rv[j] + be * pv[j];
-  P.store(cb, pv);
+  for (int k = 0; k < RPT; ++k) {
+    const int r = it.r0 + k;
+    if (!it.valid || !b_active<COH>(a, it.L, r)) continue;
+    const BLat* L = it.L;
+    const long stride = L->g.Vh * L->nr;
+    const long e = it.cb * L->nr + r;
+    const float be = (float)(COH ? __ldcg(&a.st[L->sys0 + r].beta) : a.st[L->sys0 + r].beta);
+    SpIL P{L->f[BF_P], stride, L->nr, r};
+    cpx<float> pv[12], rv[12];
+    bload<COH>(L->f[BF_P], stride, e, pv);
+    bload<COH>(L->f[BF_R], stride, e, rv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) pv[j] = rv[j] + be * pv[j];
+    P.store(it.cb, pv);
+  }
 }
+__global__ void __launch_bounds__(256) k_bpupdate(BArgs a) { bpupdate_body<1>(a, blockIdx.x); }
 
 // Per-system totals of the block partials, then the CG scalar step; one block
-// per system: thread t adds the partials of blocks t, t + blockDim, ... in
+// per system s: thread t adds the partials of blocks t, t + blockDim, ... in
 // order, the block adds the threads in a fixed tree (deterministic).
 // mode 0: pAp -> alpha; mode 1: |r|^2 -> beta, flags.
 constexpr int BRED_THREADS = 128;
-__global__ void __launch_bounds__(BRED_THREADS) k_breduce(const BLat* lats, int nlat, CGState* st,
-                                                          const double* partial, int mode) {
-  const int s = blockIdx.x;
+__device__ __forceinline__ void breduce_body(const BLat* lats, int nlat, CGState* st, const double* partial,
+                                             int mode, int s) {
   int l = 0;
   while (l < nlat && s >= lats[l].sys0 + lats[l].nr) ++l;
   if (l >= nlat || s < lats[l].sys0) return;     // the same for the whole block
   CGState& S = st[s];
-  if (S.flag != 0) return;                        // read before thread 0 may change it
+  if (__ldcg(&S.flag) != 0) return;               // read before thread 0 may change it
   const BLat& L = lats[l];
   const int r = s - L.sys0;
   double v[1] = {0.0};
-  for (int b = threadIdx.x; b < L.nblocks; b += blockDim.x) v[0] += partial[(long)(L.block0 + b) * B_MAXR + r];
+  for (int b = threadIdx.x; b < L.nblocks; b += blockDim.x) v[0] += __ldcg(partial + (long)(L.block0 + b) * B_MAXR + r);
   __shared__ double sh[32];
   block_sum<1>(v, sh);
   if (threadIdx.x != 0) return;
@@ -295,6 +340,105 @@ __global__ void __launch_bounds__(BRED_THREADS) k_breduce(const BLat* lats, int 
     if (tot <= S.upd_rr) S.flag |= FLAG_UPDATE;
     if (S.iter >= S.maxiter) S.flag |= FLAG_MAXITER;
   }
+}
+__global__ void __launch_bounds__(BRED_THREADS) k_breduce(const BLat* lats, int nlat, CGState* st,
+                                                          const double* partial, int mode) {
+  breduce_body(lats, nlat, st, partial, mode, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent CG: one cooperative launch runs `iters` CG iterations of every
+// system.  Its phases are the launches of an iteration of the graph path
+// (hop, hop + pAp sums, per-system reduce, hop, hop, update + |r|^2 sums,
+// reduce, p update), each looping over the same blocks of the layout (or over
+// the systems), separated by grid barriers.  A cooperative launch keeps every
+// block resident, so the barrier cannot wait on a block that never runs; each
+// wait is still bounded (2 s) and an expiry ends the kernel with bit 1 of the
+// batch's error word set.
+struct GridBar {
+  unsigned count, gen;
+};
+constexpr long long B_WAIT_NS = 2000000000LL;
+
+__device__ __forceinline__ long long b_gtimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// all blocks arrive; false if the wait expired (then every block leaves)
+__device__ __forceinline__ bool grid_barrier(GridBar* g, unsigned& gen, unsigned* kerr) {
+  __shared__ int ok_sh;
+  __syncthreads();                               // the block's writes happen before thread 0 arrives
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    if (atomicAdd(&g->count, 1u) == gridDim.x - 1) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicExch(&g->gen, target);                // releases the others
+    } else {
+      const long long t0 = b_gtimer();
+      for (unsigned k = 1; *(volatile unsigned*)&g->gen != target; ++k) {
+        if ((k & 255u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
+          ok = 0;
+          atomicOr(kerr, 2u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    gen = target;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+template <bool R12, int RPT>
+__global__ void __launch_bounds__(256) k_bcg_chunk(BArgs a, int nlat, int nsys, int nvb, int iters, GridBar* gb,
+                                                   unsigned* kerr) {
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = *(volatile unsigned*)&gb->gen;   // before the first arrival of any block
+  a.use_flags = 1;
+#define WD_BSYNC() \
+  if (!grid_barrier(gb, gen, kerr)) return
+  for (int it = 0; it < iters; ++it) {
+    a.out_par = 1;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) bhop_body<false, false, false, R12, RPT, true>(a, vb, BF_P, BF_T1, -1);
+    WD_BSYNC();
+    a.out_par = 0;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+      bhop_body<false, true, true, R12, RPT, true>(a, vb, BF_T1, BF_T2, BF_P);
+      __syncthreads();                             // the block's partial-sum buffer is reused
+    }
+    WD_BSYNC();
+    for (int sy = blockIdx.x; sy < nsys; sy += gridDim.x) {
+      breduce_body(a.lats, nlat, a.st, a.partial, 0, sy);
+      __syncthreads();
+    }
+    WD_BSYNC();
+    a.out_par = 1;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) bhop_body<true, false, false, R12, RPT, true>(a, vb, BF_T2, BF_T1, -1);
+    WD_BSYNC();
+    a.out_par = 0;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) bhop_body<true, true, false, R12, RPT, true>(a, vb, BF_T1, BF_AP, BF_T2);
+    WD_BSYNC();
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+      bupdate_body<RPT, true>(a, vb);
+      __syncthreads();
+    }
+    WD_BSYNC();
+    for (int sy = blockIdx.x; sy < nsys; sy += gridDim.x) {
+      breduce_body(a.lats, nlat, a.st, a.partial, 1, sy);
+      __syncthreads();
+    }
+    WD_BSYNC();
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) bpupdate_body<RPT, true>(a, vb);
+    WD_BSYNC();
+  }
+#undef WD_BSYNC
 }
 
 // one system's slot of an interleaved field <-> a standard FP64 half spinor
@@ -355,6 +499,10 @@ struct wd_batch {
   long long launches = 0;
   int in_cg = 0;                 // launches belong to a CG iteration
   std::vector<void*> mem;
+  GridBar* gbar = nullptr;       // grid barrier of the persistent CG kernel
+  unsigned* kerr = nullptr;      // device error word: bit 1 = a grid-barrier wait expired
+  int coop_grid = 0;             // resident blocks of the persistent kernel (0: not known yet)
+  int coop_rpt = 0;              // the rhs-per-thread its grid was computed for
 };
 
 namespace wd {
@@ -526,6 +674,45 @@ static int b_autotune(wd_batch* b) {
   return WD_OK;
 }
 
+// Persistent mode: the resident grid of the cooperative kernel for the
+// batch's tile shape (all blocks must fit at once), computed once per shape.
+template <bool R12, int RPT>
+static int b_coop_grid(wd_batch* b, int threads) {
+  int per_sm = 0;
+  WD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcg_chunk<R12, RPT>, threads, 0));
+  int dev = 0, nsm = 0;
+  WD_CUDA(cudaGetDevice(&dev));
+  WD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return fail(WD_ERR_ARG, "wd_batch_cg: the persistent kernel does not fit on an SM");
+  b->coop_grid = std::max(1, std::min(per_sm * nsm, std::max(b->nblocks, b->S)));
+  return WD_OK;
+}
+static int b_coop_prepare(wd_batch* b) {
+  if (b->coop_grid > 0 && b->coop_rpt == b->rpt) return WD_OK;
+  const bool r12 = b->lat_h[0].recon == 12;
+  const int t = b->threads / b->rpt;
+  int s;
+  if (r12) s = b->rpt == 4 ? b_coop_grid<true, 4>(b, t) : b->rpt == 2 ? b_coop_grid<true, 2>(b, t) : b_coop_grid<true, 1>(b, t);
+  else s = b->rpt == 4 ? b_coop_grid<false, 4>(b, t) : b->rpt == 2 ? b_coop_grid<false, 2>(b, t) : b_coop_grid<false, 1>(b, t);
+  if (s == WD_OK) b->coop_rpt = b->rpt;
+  return s;
+}
+// one chunk of `iters` CG iterations of every system in one cooperative launch
+static int b_coop_chunk(wd_batch* b, int iters) {
+  WD_CUDA(cudaMemsetAsync(b->gbar, 0, sizeof(GridBar), b->stream));   // a clean barrier for every launch
+  BArgs a = b_args(b, 0);
+  int nlat = (int)b->lat_h.size(), nsys = b->S, nvb = b->nblocks;
+  void* args[] = {&a, &nlat, &nsys, &nvb, &iters, &b->gbar, &b->kerr};
+  const dim3 grid(b->coop_grid), block(b->threads / b->rpt);
+  const bool r12 = b->lat_h[0].recon == 12;
+  void* k;
+  if (r12) k = b->rpt == 4 ? (void*)k_bcg_chunk<true, 4> : b->rpt == 2 ? (void*)k_bcg_chunk<true, 2> : (void*)k_bcg_chunk<true, 1>;
+  else k = b->rpt == 4 ? (void*)k_bcg_chunk<false, 4> : b->rpt == 2 ? (void*)k_bcg_chunk<false, 2> : (void*)k_bcg_chunk<false, 1>;
+  WD_CUDA(cudaLaunchCooperativeKernel(k, grid, block, args, 0, b->stream));
+  b->launches += 1;
+  return WD_OK;
+}
+
 }  // namespace wd
 
 extern "C" {
@@ -570,6 +757,9 @@ int wd_batch_create(wd_ctx* const* ctxs, int nlat, const double* kappas, const i
   if (e == cudaSuccess) e = cudaMalloc(&b->st_d, sizeof(CGState) * b->S);
   if (e == cudaSuccess) e = cudaMallocHost(&b->st_h, sizeof(CGState) * b->S);
   if (e == cudaSuccess) e = cudaMemset(b->st_d, 0, sizeof(CGState) * b->S);
+  if (e == cudaSuccess) e = cudaMalloc(&b->gbar, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMalloc(&b->kerr, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(b->kerr, 0, sizeof(unsigned));
   if (e != cudaSuccess) return bail(cuda_fail(e, "wd_batch_create: allocation"));
   if (ctxs[0]->stream == nullptr) {   // the legacy stream cannot be captured: use our own
     e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
@@ -595,6 +785,8 @@ int wd_batch_destroy(wd_batch* b) {
   cudaFree(b->block_lat_d);
   cudaFree(b->partial);
   cudaFree(b->st_d);
+  cudaFree(b->gbar);
+  cudaFree(b->kerr);
   if (b->st_h) cudaFreeHost(b->st_h);
   if (b->own_stream) {
     cudaStreamDestroy(b->stream);
@@ -662,8 +854,11 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
     // tune on K_hat p (p = b: real data); the pAp it leaves is recomputed
     WD_TRY(b_autotune(b));
   }
-  // a chunk of iterations, optionally as one CUDA graph
-  if (use_graph && (b->graph == nullptr || b->graph_iters != check)) {
+  // a chunk of iterations: one persistent cooperative launch (use_graph == 2),
+  // or the iterations' launches as one CUDA graph (1), or plain launches (0)
+  const bool persistent = use_graph == 2;
+  if (persistent) WD_TRY(b_coop_prepare(b));
+  if (use_graph == 1 && (b->graph == nullptr || b->graph_iters != check)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -685,7 +880,9 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
   const int per_iter = 8;
   int status = WD_OK;
   for (;;) {
-    if (use_graph) {
+    if (persistent) {
+      WD_TRY(b_coop_chunk(b, check));
+    } else if (use_graph) {
       WD_CUDA(cudaGraphLaunch(b->graph, b->stream));
       b->launches += (long long)per_iter * check;
     } else {
@@ -693,7 +890,14 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
     }
     for (int l = 0; l < nlat; ++l) b->ctx[l]->nmat += (long long)check * b->lat_h[l].nr;
     WD_CUDA(cudaMemcpyAsync(b->st_h, b->st_d, sizeof(CGState) * b->S, cudaMemcpyDeviceToHost, b->stream));
+    unsigned kerr_h = 0;
+    if (persistent) WD_CUDA(cudaMemcpyAsync(&kerr_h, b->kerr, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
     WD_CUDA(cudaStreamSynchronize(b->stream));
+    if (kerr_h != 0) {
+      WD_CUDA(cudaMemsetAsync(b->kerr, 0, sizeof(unsigned), b->stream));
+      WD_TRY(b_leave(b));
+      return fail(WD_ERR_TIMEOUT, "wd_batch_cg: a grid-barrier wait of the persistent kernel expired");
+    }
     bool all_done = true, changed = false;
     for (int l = 0; l < nlat && status == WD_OK; ++l) {
       const BLat& L = b->lat_h[l];

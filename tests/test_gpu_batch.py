@@ -8,7 +8,8 @@ in FP64 or double-float, reaches the FP64 true residual 1e-10 recomputed by
 the oracle and matches the single-system solve (1e-8).  A second
 small batch with four right-hand sides per lattice runs the batched K_hat in
 every tile shape (64-256 items per block, one, two or four right-hand sides per
-thread of the hop; 2e-5 per site) and CG with two and four per thread (1e-10).
+thread of the hop; 2e-5 per site) and CG with two and four per thread, as
+graph-replayed launches and as the persistent cooperative kernel (1e-10).
 
 The batched workload at full size (24 lattices: 8 x 8^4, 8 x 12^3 x 24,
 8 x 16^3 x 32, links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian
@@ -71,8 +72,8 @@ def torch_zeros_like(x):
     return torch.zeros_like(x)
 
 
-@pytest.mark.parametrize("use_graph,resid", [(True, 0), (False, 0), (True, 1)],
-                         ids=["graph", "eager", "graph-dfresid"])
+@pytest.mark.parametrize("use_graph,resid", [(1, 0), (0, 0), (1, 1), (2, 0), (2, 1)],
+                         ids=["graph", "eager", "graph-dfresid", "persistent", "persistent-dfresid"])
 def test_batched_cg(small, use_graph, resid):
     spec, items, batch, wd, gu = small
     bs = [_pack_rhs(it[1], gu, it[2]) for it in items]
@@ -133,15 +134,18 @@ def test_batched_khat_every_tile_shape(small4, shape):
             assert gu.site_rel_err(got, wilson.apply_Khat(U, rhs[r], k), 0, dims) < 2e-5
 
 
-@pytest.mark.parametrize("shape", [(128, 2), (128, 4)], ids=["128x2", "128x4"])
-def test_batched_cg_multi_rhs_per_thread(small4, shape):
+@pytest.mark.parametrize("shape,mode", [((128, 2), 1), ((128, 4), 1), ((128, 1), 2), ((128, 2), 2), ((64, 4), 2)],
+                         ids=["128x2-graph", "128x4-graph", "128x1-persistent", "128x2-persistent",
+                              "64x4-persistent"])
+def test_batched_cg_multi_rhs_per_thread(small4, shape, mode):
     """CG with the stop flags per system: right-hand sides of one thread converge
-    at different iterations, so each thread writes only its running systems."""
+    at different iterations, so each thread writes only its running systems;
+    graph-replayed launches and the persistent cooperative kernel."""
     spec, items, batch, wd, gu = small4
     batch.wd_batch_set_shape(*shape)
     bs = [_pack_rhs(it[1], gu, it[2]) for it in items]
     xs = [torch_zeros_like(b) for b in bs]
-    infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), True)
+    infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), mode)
     s = 0
     for (dims, a, k, nr), (U, lat, rhs), x in zip(spec, items, xs):
         for r in range(nr):
