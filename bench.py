@@ -53,11 +53,12 @@ LEVELS = [(0, 10), (1, 1), (-1, 2)]
 # double-float (2 x FP32, about 44-48 bits; b, x, r and dots stay FP64).
 # At this volume the double-float hop takes 0.50-0.58 ms against 2.08 ms in FP64.
 RESIDUAL_MODE = 1
-# K_hat applications of one trajectory of the default workload: the mean of the
-# library's N_mat counter over 20 trajectories of this seeded chain (20,256).  The
+# K_hat applications of one trajectory of the default workload: the library's
+# N_mat counter over the timed trajectories of `python bench.py` (two after three
+# warm-ups: 18,710; 18,710-18,800 in other runs of the same seeded chain).  The
 # reference arm, which runs no GPU code, scales its per-K_hat time by it; the GPU
 # arm's CPU baseline uses the count of its own run.
-N_MAT_PER_TRAJ = 20256
+N_MAT_PER_TRAJ = 18710
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hop_f32_c5_32x32x32x64.md")
 
 
