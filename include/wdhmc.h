@@ -304,6 +304,13 @@ int gaussian_draw(wd_ctx* ctx, int what, int parity, uint64_t seed, uint64_t str
 /* The Metropolis test of Section 2: accept iff u < exp(-dH), u in [0, 1) (else
  * WD_ERR_ARG); host-only, no device work. */
 int metropolis(double dH, double u, int* accept);
+/* The same test with u drawn from (seed, counter), the caller's position in
+ * its accept/reject stream: u = ((x0 >> 11) + 1/2) 2^-53 with x0 the first word
+ * of the Philox4x64-10 block of key (seed, 0) and counter (counter,
+ * WD_METROPOLIS_STREAM, 0, 0), the generator of gaussian_draw on a stream of
+ * its own.  u (may be NULL) receives the draw.  Host-only, no device work. */
+#define WD_METROPOLIS_STREAM 0x8000000000000000ull
+int metropolis_philox(double dH, uint64_t seed, uint64_t counter, double* u, int* accept);
 
 /* Cost of an action over n trajectories (Section 3.1, the cost metric):
  * C = <N_mat> / P_acc, N_mat the K_hat multiplications of one trajectory

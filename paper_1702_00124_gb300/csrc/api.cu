@@ -416,6 +416,41 @@ int metropolis(double dH, double u, int* accept) {
   return WD_OK;
 }
 
+}  // extern "C"
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) on the host: ten rounds of
+// two 64 x 64 -> 128-bit products with the published multipliers, the key
+// bumped by the published Weyl constants between rounds.
+static void host_philox4x64(uint64_t (&x)[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const unsigned __int128 p0 = (unsigned __int128)M0 * x[0], p1 = (unsigned __int128)M1 * x[2];
+    const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    const uint64_t n0 = hi1 ^ x[1] ^ k0, n2 = hi0 ^ x[3] ^ k1;
+    x[0] = n0;
+    x[1] = lo1;
+    x[2] = n2;
+    x[3] = lo0;
+  }
+}
+
+extern "C" {
+
+int metropolis_philox(double dH, uint64_t seed, uint64_t counter, double* u, int* accept) {
+  CHECK_PTR(accept);
+  uint64_t x[4] = {counter, WD_METROPOLIS_STREAM, 0ull, 0ull};
+  host_philox4x64(x, seed, 0ull);
+  const double uu = ((double)(x[0] >> 11) + 0.5) * 0x1.0p-53;
+  if (u) *u = uu;
+  return metropolis(dH, uu, accept);
+}
+
 int wd_cost(const long long* n_mat, const int* accepted, const double* dH, int n, wd_cost_result* out) {
   CHECK_PTR(n_mat);
   CHECK_PTR(accepted);

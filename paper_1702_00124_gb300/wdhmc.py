@@ -110,6 +110,7 @@ _SIG = {
     "kinetic_energy": ([_P, _P, C.POINTER(_D)], _I),
     "gaussian_draw": ([_P, _I, _I, C.c_uint64, C.c_uint64, _P], _I),
     "metropolis": ([_D, _D, C.POINTER(_I)], _I),
+    "metropolis_philox": ([_D, C.c_uint64, C.c_uint64, C.POINTER(_D), C.POINTER(_I)], _I),
     "wd_cost": ([C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_D), _I, C.POINTER(wd_cost_result)], _I),
     "hmc_trajectory": ([_P, C.POINTER(wd_hmc_params), _D, C.POINTER(wd_hmc_result)], _I),
     "hmc_trajectory_host": ([_P, C.POINTER(wd_hmc_params), _D, _P, _P, C.POINTER(wd_hmc_result)], _I),
@@ -218,6 +219,13 @@ def metropolis(dH, u):
     a = C.c_int(0)
     _check(lib.metropolis(dH, u, C.byref(a)))
     return bool(a.value)
+
+
+def metropolis_philox(dH, seed, counter):
+    """(accepted, u) with u drawn from (seed, counter) by Philox4x64-10."""
+    a, u = C.c_int(0), C.c_double(0)
+    _check(lib.metropolis_philox(dH, seed, counter, C.byref(u), C.byref(a)))
+    return bool(a.value), u.value
 
 
 def wd_cost(n_mat, accepted, dH):

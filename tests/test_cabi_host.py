@@ -96,6 +96,22 @@ def test_metropolis_host(wd):
         wd.metropolis(0.1, 1.5)
 
 
+def test_metropolis_from_seed_and_counter(wd):
+    """u of the (seed, counter) form is the oracle's Philox4x64-10 draw
+    (first word of counter (counter, 2^63, 0, 0) under key (seed, 0)), bit for
+    bit, and the decision is u < exp(-dH)."""
+    from oracle import philox
+    rng = np.random.default_rng(5)
+    for seed, counter in [(0, 0), (170200124, 7), (2**64 - 1, 2**63 + 5)] + \
+            [(int(a), int(b)) for a, b in rng.integers(0, 2**63, size=(6, 2), dtype=np.int64)]:
+        x0 = philox.philox4x64_10(counter, 2**63, 0, 0, seed, 0)[0]
+        u_ref = (float(int(x0) >> 11) + 0.5) * 2.0**-53
+        for dH in (-0.3, 0.0, 0.7, 5.0):
+            acc, u = wd.metropolis_philox(dH, seed, counter)
+            assert u == u_ref
+            assert acc == (u_ref < np.exp(-dH))
+
+
 def test_cost_matches_oracle(wd):
     """wd_cost (C = N_mat / P_acc, Section 3.1) against the oracle's definition on
     seeded trajectory records, and its argument checks."""
