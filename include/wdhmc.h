@@ -459,14 +459,18 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
  * counterpart in the paper). */
 int wd_batch_info(wd_batch* b, int* n_systems, int* threads, long long* launches);
 /* Tile shape of the batched kernels chosen by the tuner (no counterpart in the
- * paper): (site, rhs) items per block, and right-hand sides of one site that
- * one thread of the batched hop applies its link to (1, 2 or 4; the link is
- * loaded and rebuilt once for them).  Either pointer may be NULL. */
-int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread);
+ * paper): (site, rhs) items per block; right-hand sides of one site that one
+ * thread of the batched hop applies its link to (1, 2 or 4; the link is loaded
+ * and rebuilt once for them); link_staging = 1 when the hop runs on the
+ * per-thread pipeline that copies each thread's links two directions ahead
+ * into shared memory (128 items, one rhs per thread, 12-real links).  Any
+ * pointer may be NULL. */
+int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread, int* link_staging);
 /* Fix the tile shape instead of tuning it (no counterpart in the paper):
  * items_per_block 64, 128 or 256; rhs_per_thread 1, 2 or 4 dividing every
- * lattice's nrhs.  WD_ERR_ARG otherwise; the batch is unchanged then. */
-int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread);
+ * lattice's nrhs; link_staging 0 or 1 (1 needs 128 items, one rhs per thread
+ * and 12-real links).  WD_ERR_ARG otherwise; the batch is unchanged then. */
+int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread, int link_staging);
 
 /* ---- allocation-free K_hat ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

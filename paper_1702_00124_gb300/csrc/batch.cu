@@ -19,7 +19,7 @@
 #include <cmath>
 #include <new>
 
-#include "dslash_impl.cuh"
+#include "dslash_staged.cuh"
 
 namespace wd {
 
@@ -244,6 +244,52 @@ __device__ __forceinline__ void bhop_body(const BArgs& a, int vb, int fin, int f
 template <bool DAG, bool XPAY, bool NORM, bool R12, int RPT>
 __global__ void __launch_bounds__(256) k_bhop(BArgs a, int fin, int fout, int fy) {
   bhop_body<DAG, XPAY, NORM, R12, RPT>(a, blockIdx.x, fin, fout, fy);
+}
+
+// The batched hop on the single-lattice stencil's per-thread pipeline (one
+// (site, rhs) item per thread, 12-real links): the links of the next two
+// directions are copied into shared memory by cp.async while the current one
+// is computed (dslash_staged.cuh); the item's lattice supplies geometry, links
+// and fields.  Blocks of HOP_ST_THREADS items.
+template <bool DAG, bool XPAY, bool NORM>
+__global__ void __launch_bounds__(HOP_ST_THREADS, HOP_MINB) k_bhop_st(BArgs a, int fin, int fout, int fy) {
+  extern __shared__ float4 sbuf[];
+  const BItem it = b_item(a, blockIdx.x, 1);
+  const BLat* L = it.L;
+  float v[B_MAXR];
+#pragma unroll
+  for (int k = 0; k < B_MAXR; ++k) v[k] = 0.f;
+  if (it.valid && b_active<false>(a, L, it.r0)) {
+    const long stride = L->g.Vh * L->nr;
+    const int r = it.r0;
+    const SpIL in{L->f[fin], stride, L->nr, r}, out{L->f[fout], stride, L->nr, r};
+    using HA = HopArgs<SpIL, SpIL, SpIL, GF32R12>;
+    const HA ha{L->g, a.out_par, in, out, in, GF32R12{L->g12, L->g.Vh}, 0.0, Reduce{nullptr, nullptr, nullptr},
+                nullptr};
+    Staged<HOP_NST, DAG, HA> S{ha, it.cb, {0, 0, 0, 0}, sbuf, (int)threadIdx.x, (int)blockDim.x};
+    L->g.coords(it.cb, a.out_par, S.c);
+    cpx<float> acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = mk<float>(0, 0);
+    S.run(acc);
+    if constexpr (XPAY) {
+      cpx<float> yv[12];
+      SpIL{L->f[fy], stride, L->nr, r}.loadT(it.cb, yv);
+      const float al = (float)(-L->kappa * L->kappa);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) acc[j] = yv[j] + al * acc[j];
+    }
+    if constexpr (NORM) {
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) q = fmaf(acc[j].r, acc[j].r, fmaf(acc[j].i, acc[j].i, q));
+#pragma unroll
+      for (int m = 0; m < B_MAXR; ++m)
+        if (m == r) v[m] = q;
+    }
+    out.store(it.cb, acc);
+  }
+  if constexpr (NORM) b_block_partial(a, blockIdx.x, v);
 }
 
 // x += alpha p; r -= alpha Ap; partial |r|^2 (RPT items per thread)
@@ -484,6 +530,7 @@ struct wd_batch {
   int S = 0;                     // systems
   int threads = 128;             // items (site, rhs) per block (autotuned on first use)
   int rpt = 1;                   // right-hand sides per thread of the batched hop (autotuned)
+  int staged = 0;                // 1: the hop on the per-thread link-staging pipeline (rpt 1, 128 items)
   bool tuned = false;
   std::vector<int> block_lat_h;
   int* block_lat_d = nullptr;
@@ -546,7 +593,18 @@ static int b_hop(wd_batch* b, int out_par, bool dag, int fin, int fout, int fy, 
     else if (b->rpt == 2) k_bhop<D, X, N, R, 2><<<b->nblocks, b->threads / 2, 0, b->stream>>>(a, fin, fout, fy); \
     else k_bhop<D, X, N, R, 1><<<b->nblocks, b->threads, 0, b->stream>>>(a, fin, fout, fy);                \
   } while (0)
-  if (r12) {
+  if (r12 && b->staged) {
+#define WD_BS(D, X, N) k_bhop_st<D, X, N><<<b->nblocks, HOP_ST_THREADS, HOP_STAGE_SMEM, b->stream>>>(a, fin, fout, fy)
+    if (!dag) {
+      if (fy < 0) WD_BS(false, false, false);
+      else if (norm) WD_BS(false, true, true);
+      else WD_BS(false, true, false);
+    } else {
+      if (fy < 0) WD_BS(true, false, false);
+      else WD_BS(true, true, false);
+    }
+#undef WD_BS
+  } else if (r12) {
     if (!dag) {
       if (fy < 0) WD_BH(false, false, false, true);
       else if (norm) WD_BH(false, true, true, true);
@@ -627,14 +685,15 @@ static int b_leave(wd_batch* b) {
 // (128 items, one rhs per thread) is replaced only by a candidate at least 3 %
 // faster.  A shape with rpt > 1 needs nr % rpt == 0 on every lattice.
 struct BShape {
-  int threads, rpt;
+  int threads, rpt, staged;
 };
 static int b_autotune(wd_batch* b) {
   constexpr int ROUNDS = 5;
-  const BShape all[] = {{128, 1}, {256, 1}, {64, 1}, {128, 2}, {256, 2}, {128, 4}, {256, 4}};
+  const BShape all[] = {{128, 1, 0}, {256, 1, 0}, {64, 1, 0}, {128, 2, 0}, {256, 2, 0},
+                        {128, 4, 0}, {256, 4, 0}, {HOP_ST_THREADS, 1, 1}};
   std::vector<BShape> cand;
   for (const BShape& c : all) {
-    bool ok = true;
+    bool ok = !c.staged || b->lat_h[0].recon == 12;
     for (const BLat& L : b->lat_h) ok = ok && (L.nr % c.rpt == 0);
     if (ok) cand.push_back(c);
   }
@@ -649,6 +708,7 @@ static int b_autotune(wd_batch* b) {
       const int k = (j + r) % NC;
       WD_TRY(b_layout(b, cand[k].threads));
       b->rpt = cand[k].rpt;
+      b->staged = cand[k].staged;
       cudaEventRecord(e0, b->stream);
       WD_TRY(b_khat(b, BF_P, BF_AP, false));
       cudaEventRecord(e1, b->stream);
@@ -670,6 +730,7 @@ static int b_autotune(wd_batch* b) {
     if (med[k] < 0.97f * med[pick]) pick = k;
   WD_TRY(b_layout(b, cand[pick].threads));
   b->rpt = cand[pick].rpt;
+  b->staged = cand[pick].staged;
   b->tuned = true;
   return WD_OK;
 }
@@ -976,8 +1037,11 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
   return status;
 }
 
-int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread) {
+int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread, int link_staging) {
   if (!b) return fail(WD_ERR_ARG, "null batch");
+  if (link_staging != 0 && link_staging != 1) return fail(WD_ERR_ARG, "wd_batch_set_shape: link_staging must be 0 or 1");
+  if (link_staging && (items_per_block != HOP_ST_THREADS || rhs_per_thread != 1 || b->lat_h[0].recon != 12))
+    return fail(WD_ERR_ARG, "wd_batch_set_shape: link staging needs 128 items per block, one rhs per thread, 12-real links");
   if (items_per_block != 64 && items_per_block != 128 && items_per_block != 256)
     return fail(WD_ERR_ARG, "wd_batch_set_shape: items_per_block must be 64, 128 or 256");
   if (rhs_per_thread != 1 && rhs_per_thread != 2 && rhs_per_thread != 4)
@@ -987,14 +1051,16 @@ int wd_batch_set_shape(wd_batch* b, int items_per_block, int rhs_per_thread) {
       return fail(WD_ERR_ARG, "wd_batch_set_shape: rhs_per_thread must divide every lattice's nrhs");
   WD_TRY(b_layout(b, items_per_block));
   b->rpt = rhs_per_thread;
+  b->staged = link_staging;
   b->tuned = true;
   return WD_OK;
 }
 
-int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread) {
+int wd_batch_shape(wd_batch* b, int* items_per_block, int* rhs_per_thread, int* link_staging) {
   if (!b) return fail(WD_ERR_ARG, "null batch");
   if (items_per_block) *items_per_block = b->threads;
   if (rhs_per_thread) *rhs_per_thread = b->rpt;
+  if (link_staging) *link_staging = b->staged;
   return WD_OK;
 }
 

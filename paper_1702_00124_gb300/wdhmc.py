@@ -137,8 +137,8 @@ _SIG = {
     "wd_batch_mdagm": ([_P, C.POINTER(_P), C.POINTER(_P)], _I),
     "wd_batch_cg": ([_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(wd_cg_params), _I, C.POINTER(wd_cg_info)], _I),
     "wd_batch_info": ([_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)], _I),
-    "wd_batch_shape": ([_P, C.POINTER(_I), C.POINTER(_I)], _I),
-    "wd_batch_set_shape": ([_P, _I, _I], _I),
+    "wd_batch_shape": ([_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)], _I),
+    "wd_batch_set_shape": ([_P, _I, _I, _I], _I),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(lib, _name)
@@ -282,13 +282,13 @@ class Batch:
         _check(lib.wd_batch_info(self.h, C.byref(s), C.byref(t), C.byref(n)))
         return dict(systems=s.value, threads=t.value, launches=n.value)
 
-    def wd_batch_set_shape(self, items_per_block, rhs_per_thread):
-        _check(lib.wd_batch_set_shape(self.h, items_per_block, rhs_per_thread))
+    def wd_batch_set_shape(self, items_per_block, rhs_per_thread, link_staging=0):
+        _check(lib.wd_batch_set_shape(self.h, items_per_block, rhs_per_thread, int(link_staging)))
 
     def wd_batch_shape(self):
-        t, r = C.c_int(0), C.c_int(0)
-        _check(lib.wd_batch_shape(self.h, C.byref(t), C.byref(r)))
-        return dict(items_per_block=t.value, rhs_per_thread=r.value)
+        t, r, st = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(lib.wd_batch_shape(self.h, C.byref(t), C.byref(r), C.byref(st)))
+        return dict(items_per_block=t.value, rhs_per_thread=r.value, link_staging=st.value)
 
 
 class Lattice:

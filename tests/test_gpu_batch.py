@@ -8,8 +8,9 @@ in FP64 or double-float, reaches the FP64 true residual 1e-10 recomputed by
 the oracle and matches the single-system solve (1e-8).  A second
 small batch with four right-hand sides per lattice runs the batched K_hat in
 every tile shape (64-256 items per block, one, two or four right-hand sides per
-thread of the hop; 2e-5 per site) and CG with two and four per thread, as
-graph-replayed launches and as the persistent cooperative kernel (1e-10).
+thread of the hop, or the per-thread link-staging pipeline; 2e-5 per site) and
+CG with two and four per thread and with link staging, as graph-replayed
+launches and as the persistent cooperative kernel (1e-10).
 
 The batched workload at full size (24 lattices: 8 x 8^4, 8 x 12^3 x 24,
 8 x 16^3 x 32, links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian
@@ -26,9 +27,10 @@ from paper_1702_00124_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 
-def _make(dims, a, kappa, nr, seed, wd, gu, stream):
+def _make(dims, a, kappa, nr, seed, wd, gu, stream, recon=0):
     U = synthetic.gauge_field(dims, a, seed)
     lat = wd.Lattice(dims, stream=stream)
+    lat.wd_set_recon(recon)
     lat.wd_gauge_load(gu.dev(U))
     rhs = [lattice.mask(synthetic.spinor_field(dims, seed + 1 + r), dims, 0) for r in range(nr)]
     return U, lat, rhs
@@ -101,14 +103,15 @@ def test_batched_cg(small, use_graph, resid):
 
 @pytest.fixture(scope="module")
 def small4():
-    """Three uneven lattices with four right-hand sides each: every tile shape
-    (one, two or four right-hand sides per thread of the batched hop) applies."""
+    """Three uneven lattices with four right-hand sides each and 12-real links:
+    every tile shape (one, two or four right-hand sides per thread of the
+    batched hop, or the link-staging pipeline) applies."""
     import torch
     from paper_1702_00124_gb300 import wdhmc as wd
     from tests import gpu_util as gu
     spec = [((4, 4, 4, 4), 0.5, 0.12, 4), ((6, 4, 6, 10), 0.4, 0.128, 4), ((8, 8, 8, 8), 0.4, 0.125, 4)]
     stream = torch.cuda.current_stream()
-    items = [_make(d, a, k, nr, 1900 + 10 * i, wd, gu, stream) for i, (d, a, k, nr) in enumerate(spec)]
+    items = [_make(d, a, k, nr, 1900 + 10 * i, wd, gu, stream, wd.RECON_12) for i, (d, a, k, nr) in enumerate(spec)]
     lats = [it[1] for it in items]
     batch = wd.Batch(lats, [s[2] for s in spec], [s[3] for s in spec])
     yield spec, items, batch, wd, gu
@@ -117,14 +120,14 @@ def small4():
         lat.close()
 
 
-SHAPES = [(128, 1), (64, 1), (256, 1), (128, 2), (256, 2), (128, 4), (256, 4)]
+SHAPES = [(128, 1, 0), (64, 1, 0), (256, 1, 0), (128, 2, 0), (256, 2, 0), (128, 4, 0), (256, 4, 0), (128, 1, 1)]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=[f"{t}x{r}" for t, r in SHAPES])
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{t}x{r}" + ("-staged" if st else "") for t, r, st in SHAPES])
 def test_batched_khat_every_tile_shape(small4, shape):
     spec, items, batch, wd, gu = small4
     batch.wd_batch_set_shape(*shape)
-    assert batch.wd_batch_shape() == dict(items_per_block=shape[0], rhs_per_thread=shape[1])
+    assert batch.wd_batch_shape() == dict(items_per_block=shape[0], rhs_per_thread=shape[1], link_staging=shape[2])
     ins = [_pack_rhs(it[1], gu, it[2]) for it in items]
     outs = [torch_zeros_like(x) for x in ins]
     batch.wd_batch_mdagm(ins, outs)
@@ -134,9 +137,10 @@ def test_batched_khat_every_tile_shape(small4, shape):
             assert gu.site_rel_err(got, wilson.apply_Khat(U, rhs[r], k), 0, dims) < 2e-5
 
 
-@pytest.mark.parametrize("shape,mode", [((128, 2), 1), ((128, 4), 1), ((128, 1), 2), ((128, 2), 2), ((64, 4), 2)],
-                         ids=["128x2-graph", "128x4-graph", "128x1-persistent", "128x2-persistent",
-                              "64x4-persistent"])
+@pytest.mark.parametrize("shape,mode", [((128, 2, 0), 1), ((128, 4, 0), 1), ((128, 1, 1), 1), ((128, 1, 0), 2),
+                                        ((128, 2, 0), 2), ((64, 4, 0), 2)],
+                         ids=["128x2-graph", "128x4-graph", "128x1-staged-graph", "128x1-persistent",
+                              "128x2-persistent", "64x4-persistent"])
 def test_batched_cg_multi_rhs_per_thread(small4, shape, mode):
     """CG with the stop flags per system: right-hand sides of one thread converge
     at different iterations, so each thread writes only its running systems;
@@ -158,7 +162,8 @@ def test_batched_cg_multi_rhs_per_thread(small4, shape, mode):
 
 def test_batched_shape_arguments_checked(small):
     spec, items, batch, wd, gu = small
-    for bad in ((96, 1), (128, 3), (128, 2)):          # nrhs 3 and 1 are not multiples of 2
+    # nrhs 3 and 1 are not multiples of 2; staging needs 12-real links, 128 items, one rhs per thread
+    for bad in ((96, 1, 0), (128, 3, 0), (128, 2, 0), (128, 1, 1), (64, 1, 1), (128, 1, 2)):
         with pytest.raises(wd.WdError) as e:
             batch.wd_batch_set_shape(*bad)
         assert e.value.code == 1
