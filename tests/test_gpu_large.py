@@ -6,7 +6,8 @@ sampled-site operator, with the tolerances of the small lattices (FP64 1e-12,
 FP32 1e-5, BF16 with per-site norm 3e-2 per site; measured BF16 maximum over
 2048 sites about 3.5e-3 for the hop and K_hat, the same as on 8^4); the force
 kernel from given X, Y at 256 sampled links (1e-12 FP64, 1e-5 FP32 per link);
-whole-lattice properties of the FP64 operator
+the tile-staged stencil's K_hat against the oracle's sampled sites and against the
+thread kernel at every site (1e-6); whole-lattice properties of the FP64 operator
 (<psi, K psi> = |M psi|^2, adjointness of M_hat, 1e-12); the mixed-precision
 solve's true residual recomputed with the FP64 operator.
 
@@ -83,6 +84,40 @@ def test_c5_khat_sampled(c5, prec, recon, tol):
         lat.wd_set_recon(0)
     idx = c5["sites"][0]
     assert _rel(got[idx], sampled.khat_at(c5["U"], f, k, idx)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (3, 3e-2)], ids=["fp32", "bf16"])
+def test_c5_tile_stencil(c5, prec, tol):
+    """The tile-staged kernel (WD_STENCIL_TILE) at the workload's volume: K_hat
+    against the oracle at the sampled sites, and against the thread kernel at
+    every site (the same FP32 operations per site: 1e-6 relative for FP32
+    spinors; BF16 inputs are quantised identically, so 1e-6 holds there too)."""
+    import torch
+    lat, gu, wd, dims = c5["lat"], c5["gu"], c5["wd"], c5["dims"]
+    k = 0.136
+    f = lattice.mask(c5["psi"], dims, 0)
+    lat.wd_set_recon(1)
+    try:
+        eo = gu.pack(lat, c5["psi"], 0)
+        outs = {}
+        for name, st in (("tile", wd.STENCIL_TILE), ("thread", wd.STENCIL_THREAD)):
+            lat.wd_set_stencil(st)
+            o = lat.half_spinor()
+            lat.mdagm_apply(k, prec, 1, eo, o)
+            outs[name] = o
+        assert lat.wd_kernel_status() == 0
+    finally:
+        lat.wd_set_stencil(wd.STENCIL_THREAD)
+        lat.wd_set_recon(0)
+    got = gu.unpack(lat, outs["tile"], 0).reshape(-1, 4, 3)
+    idx = c5["sites"][0]
+    assert _rel(got[idx], sampled.khat_at(c5["U"], f, k, idx)) < tol
+    a = torch.view_as_complex(outs["tile"].view(-1, 2)).view(12, -1)
+    b = torch.view_as_complex(outs["thread"].view(-1, 2)).view(12, -1)
+    d = torch.linalg.vector_norm(a - b, dim=0)
+    r = torch.linalg.vector_norm(b, dim=0)
+    rel = torch.max(d / torch.clamp(r, min=1e-3 * float(torch.sqrt(torch.mean(r ** 2)))))
+    assert float(rel) < 1e-6
 
 
 def test_c5_operator_properties(c5):
