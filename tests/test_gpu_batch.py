@@ -15,7 +15,8 @@ launches and as the persistent cooperative kernel (1e-10).
 The batched workload at full size (24 lattices: 8 x 8^4, 8 x 12^3 x 24,
 8 x 16^3 x 32, links exp(0.4 i H), kappa ~ U[0.125, 0.135], 4 Gaussian
 right-hand sides each): every one of the 96 systems reaches 1e-10, checked
-with each lattice's FP64 K_hat; the batched K_hat matches the oracle's
+with each lattice's FP64 K_hat, with graph-replayed launches and with the
+persistent cooperative kernel; the batched K_hat matches the oracle's
 sampled-site K_hat on one lattice of each size.
 """
 import numpy as np
@@ -190,16 +191,19 @@ def test_batched_workload_full_size():
         xs.append(torch.zeros_like(b))
         Us.append(U if i % 8 == 0 else None)
     batch = wd.Batch(lats, [w["kappa"] for w in work], [w["nrhs"] for w in work])
-    infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), True)
-    s = 0
-    for w, lat, b, x in zip(work, lats, bs, xs):
-        for r in range(w["nrhs"]):
-            sl = slice(r * 24 * lat.Vh, (r + 1) * 24 * lat.Vh)
-            Kx = lat.half_spinor()
-            lat.mdagm_apply(w["kappa"], wd.F64, 1, x[sl].contiguous(), Kx)
-            rel = float(torch.linalg.vector_norm(b[sl] - Kx) / torch.linalg.vector_norm(b[sl]))
-            assert rel <= 1.01e-10, (w["dims"], r, rel, infos[s])
-            s += 1
+    for mode in (1, 2):                                  # graph-replayed launches; persistent kernel
+        for x in xs:
+            x.zero_()
+        infos = batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), mode)
+        s = 0
+        for w, lat, b, x in zip(work, lats, bs, xs):
+            for r in range(w["nrhs"]):
+                sl = slice(r * 24 * lat.Vh, (r + 1) * 24 * lat.Vh)
+                Kx = lat.half_spinor()
+                lat.mdagm_apply(w["kappa"], wd.F64, 1, x[sl].contiguous(), Kx)
+                rel = float(torch.linalg.vector_norm(b[sl] - Kx) / torch.linalg.vector_norm(b[sl]))
+                assert rel <= 1.01e-10, (mode, w["dims"], r, rel, infos[s])
+                s += 1
     # batched K_hat against the oracle's sampled sites, one lattice per size,
     # on host-drawn inputs placed in the first right-hand side
     ins = [b.clone() for b in bs]
