@@ -879,6 +879,8 @@ int wd_batch_cg(wd_batch* b, const double* const* bvec, double* const* x, const 
                 wd_cg_info* infos) {
   if (!b || !bvec || !x || !p) return fail(WD_ERR_ARG, "wd_batch_cg: null argument");
   if (!(p->tol > 0) || p->maxiter < 1) return fail(WD_ERR_ARG, "wd_batch_cg: tol > 0 and maxiter >= 1");
+  if (use_graph < 0 || use_graph > 2)
+    return fail(WD_ERR_ARG, "wd_batch_cg: use_graph must be 0 (launches), 1 (graph) or 2 (persistent kernel)");
   const double delta = (p->delta > 0 && p->delta < 1) ? p->delta : 1e-3;
   const int check = p->check_every > 0 ? p->check_every : 16;
   const int nlat = (int)b->lat_h.size();

@@ -161,6 +161,16 @@ def test_batched_cg_multi_rhs_per_thread(small4, shape, mode):
     assert len({i["iters"] for i in infos}) > 1       # systems did stop at different iterations
 
 
+def test_batched_cg_mode_checked(small):
+    spec, items, batch, wd, gu = small
+    bs = [_pack_rhs(it[1], gu, it[2]) for it in items]
+    xs = [torch_zeros_like(b) for b in bs]
+    for bad in (-1, 3):
+        with pytest.raises(wd.WdError) as e:
+            batch.wd_batch_cg(bs, xs, wd.cg_params(tol=1e-10, prec=wd.F32), bad)
+        assert e.value.code == 1
+
+
 def test_batched_shape_arguments_checked(small):
     spec, items, batch, wd, gu = small
     # nrhs 3 and 1 are not multiples of 2; staging needs 12-real links, 128 items, one rhs per thread
